@@ -1,0 +1,256 @@
+"""CPU oracle for the threshold random hyperbolic graph -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The generator library never loads it,
+and it never loads the generator: the two share no code.  It wraps the plain C
+restatement in ``hrg_oracle.c`` with ctypes and numpy.
+
+Functions and the passage each follows (von Looz, Meyerhenke, Prutkin, Staudt,
+"Fast generation of complex networks with underlying hyperbolic geometry"):
+
+* ``philox``            -- Philox4x32-10 (Salmon et al., SC'11); the paper names no
+                           generator, this is the chosen one.
+* ``expected_degree``   -- Krioukov et al. Eq. (22) restated in Appendix B.1
+                           (reading: middle term (pi-1)(zeta/alpha), zeta = 1).
+* ``solve_radius``      -- Appendix B.1 binary search; Algorithm 1, first line.
+* ``sample``            -- Algorithm 1, the two "draw" lines; Eq. (1).
+* ``cosh_dist``         -- Sec. 2.1 edge rule, hyperbolic law of cosines.
+* ``brute_csr``         -- the plain definition: all pairs, edge iff dist < R.
+* ``band_csr`` / ``band_rows`` -- an independent band algorithm for large n.
+* ``ties``              -- pairs within 1e-12 relative of the threshold.
+
+Every function here is pinned by ``tests/test_oracle*.py`` to something other
+than itself (an independent Philox, mpmath, scipy quadrature, the paper's
+worked example, Lemma 4 cell masses, exhaustive checks).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hrg_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.c_double
+_I64 = ctypes.c_int64
+_P = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            L.orc_philox4x32_10.argtypes = [_P, _P, _P]
+            L.orc_expected_degree.argtypes = [_D, _D, _D]
+            L.orc_expected_degree.restype = _D
+            L.orc_solve_radius.argtypes = [_I64, _D, _D, _P]
+            L.orc_solve_radius.restype = ctypes.c_int
+            L.orc_uniforms.argtypes = [ctypes.c_uint64, _I64, _P, _P]
+            L.orc_sample.argtypes = [_I64, _D, _D, ctypes.c_uint64, _P, _P]
+            for f in ("orc_cosh_dist", "orc_cosh_dist_textbook", "orc_cosh_dist_poincare"):
+                getattr(L, f).argtypes = [_D, _D, _D, _D]
+                getattr(L, f).restype = _D
+            L.orc_in_circle_prop1.argtypes = [_D, _D, _D, _D, _D]
+            L.orc_in_circle_prop1.restype = ctypes.c_int
+            L.orc_brute_degrees.argtypes = [_I64, _P, _P, _D, _P]
+            L.orc_brute_degrees.restype = _I64
+            L.orc_brute_fill.argtypes = [_I64, _P, _P, _D, _P, _P]
+            L.orc_brute_ties.argtypes = [_I64, _P, _P, _D, _D, _I64, _P]
+            L.orc_brute_ties.restype = _I64
+            L.orc_bands_build.argtypes = [_I64, _P, _P, _D]
+            L.orc_bands_build.restype = _P
+            L.orc_bands_free.argtypes = [_P]
+            L.orc_bands_degrees.argtypes = [_P, _P, _P, _P]
+            L.orc_bands_degrees.restype = _I64
+            L.orc_bands_fill.argtypes = [_P, _P, _P, _P, _P]
+            L.orc_bands_rows.argtypes = [_P, _P, _P, _I64, _P, _P, _P, _P]
+            L.orc_bands_ties.argtypes = [_P, _P, _P, _D, _I64, _P]
+            L.orc_bands_ties.restype = _I64
+            L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def set_threads(t: int) -> None:
+    lib().orc_set_threads(int(t))
+
+
+def philox(ctr, key) -> np.ndarray:
+    """One Philox4x32-10 block: ctr = 4 uint32 words, key = 2 uint32 words."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    o = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
+    return o
+
+
+def uniforms(seed: int, vid: int):
+    a = ctypes.c_double()
+    b = ctypes.c_double()
+    lib().orc_uniforms(ctypes.c_uint64(seed), vid, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def expected_degree(n, alpha, R) -> float:
+    return float(lib().orc_expected_degree(float(n), float(alpha), float(R)))
+
+
+def solve_radius(n: int, alpha: float, kbar: float) -> float:
+    out = ctypes.c_double()
+    rc = lib().orc_solve_radius(int(n), float(alpha), float(kbar), ctypes.byref(out))
+    if rc != 0:
+        raise ValueError("invalid parameters for Eq. (22): n=%r alpha=%r kbar=%r" % (n, alpha, kbar))
+    return out.value
+
+
+def sample(n: int, alpha: float, R: float, seed: int):
+    r = np.empty(n, dtype=np.float64)
+    phi = np.empty(n, dtype=np.float64)
+    lib().orc_sample(int(n), float(alpha), float(R), ctypes.c_uint64(seed), _ptr(r), _ptr(phi))
+    return r, phi
+
+
+def cosh_dist(r1, phi1, r2, phi2) -> float:
+    return float(lib().orc_cosh_dist(r1, phi1, r2, phi2))
+
+
+def cosh_dist_textbook(r1, phi1, r2, phi2) -> float:
+    return float(lib().orc_cosh_dist_textbook(r1, phi1, r2, phi2))
+
+
+def cosh_dist_poincare(r1, phi1, r2, phi2) -> float:
+    return float(lib().orc_cosh_dist_poincare(r1, phi1, r2, phi2))
+
+
+def in_circle_prop1(R, rq, phiq, rc, phic) -> bool:
+    return bool(lib().orc_in_circle_prop1(R, rq, phiq, rc, phic))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _offsets(deg: np.ndarray) -> np.ndarray:
+    off = np.zeros(len(deg) + 1, dtype=np.int64)
+    np.cumsum(deg, out=off[1:])
+    return off
+
+
+def brute_csr(r, phi, R):
+    """All-pairs CSR (row_off int64[n+1], col_idx int32[2m]), rows ascending."""
+    r = _f64(r)
+    phi = _f64(phi)
+    n = len(r)
+    deg = np.zeros(n, dtype=np.int64)
+    lib().orc_brute_degrees(n, _ptr(r), _ptr(phi), float(R), _ptr(deg))
+    off = _offsets(deg)
+    col = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
+    lib().orc_brute_fill(n, _ptr(r), _ptr(phi), float(R), _ptr(off), _ptr(col))
+    return off, col[: int(off[-1])]
+
+
+class Bands:
+    """The CPU band algorithm's structure over one point set."""
+
+    def __init__(self, r, phi, R):
+        self.r = _f64(r)
+        self.phi = _f64(phi)
+        self.R = float(R)
+        self.n = len(self.r)
+        self.h = lib().orc_bands_build(self.n, _ptr(self.r), _ptr(self.phi), self.R)
+
+    def close(self):
+        if self.h:
+            lib().orc_bands_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def degrees(self):
+        deg = np.zeros(self.n, dtype=np.int64)
+        lib().orc_bands_degrees(self.h, _ptr(self.r), _ptr(self.phi), _ptr(deg))
+        return deg
+
+    def csr(self):
+        deg = self.degrees()
+        off = _offsets(deg)
+        col = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
+        lib().orc_bands_fill(self.h, _ptr(self.r), _ptr(self.phi), _ptr(off), _ptr(col))
+        return off, col[: int(off[-1])]
+
+    def rows(self, qids):
+        """Sorted neighbour lists of the vertices ``qids``: (cnt, off, rows)."""
+        q = np.ascontiguousarray(np.asarray(qids, dtype=np.int64))
+        cnt = np.zeros(len(q), dtype=np.int64)
+        lib().orc_bands_rows(self.h, _ptr(self.r), _ptr(self.phi), len(q), _ptr(q), _ptr(cnt), None, None)
+        off = _offsets(cnt)
+        rows = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
+        lib().orc_bands_rows(self.h, _ptr(self.r), _ptr(self.phi), len(q), _ptr(q), _ptr(cnt), _ptr(off), _ptr(rows))
+        return cnt, off, rows[: int(off[-1])]
+
+    def ties(self, tol=1e-12, cap=1 << 16):
+        pairs = np.zeros(2 * cap, dtype=np.int64)
+        k = lib().orc_bands_ties(self.h, _ptr(self.r), _ptr(self.phi), float(tol), cap, _ptr(pairs))
+        return int(k), pairs[: 2 * min(int(k), cap)].reshape(-1, 2)
+
+
+def band_csr(r, phi, R):
+    b = Bands(r, phi, R)
+    try:
+        return b.csr()
+    finally:
+        b.close()
+
+
+def brute_ties(r, phi, R, tol=1e-12, cap=1 << 16):
+    r = _f64(r)
+    phi = _f64(phi)
+    pairs = np.zeros(2 * cap, dtype=np.int64)
+    k = lib().orc_brute_ties(len(r), _ptr(r), _ptr(phi), float(R), float(tol), cap, _ptr(pairs))
+    return int(k), pairs[: 2 * min(int(k), cap)].reshape(-1, 2)
+
+
+def generate(n: int, alpha: float, kbar: float, seed: int, method: str = "auto", R: float | None = None):
+    """Whole oracle pipeline: R (Eq. (22) unless given), points, CSR."""
+    if R is None:
+        R = solve_radius(n, alpha, kbar)
+    r, phi = sample(n, alpha, R, seed)
+    if method == "auto":
+        method = "brute" if n <= 20000 else "bands"
+    off, col = brute_csr(r, phi, R) if method == "brute" else band_csr(r, phi, R)
+    return {"R": R, "r": r, "phi": phi, "row_off": off, "col_idx": col}

@@ -1,0 +1,73 @@
+"""Seeded synthetic workloads shared by the tests, the smoke check and the bench.
+
+This module holds inputs only: parameter sets and numpy-seeded point sets.  It
+contains none of the generator's arithmetic (no radius solve, no sampler, no
+predicate), so both the CUDA path and the CPU oracle can take their inputs
+from it without sharing any of the method's code.
+
+The paper measures on graphs it generates itself (Sec. 4.4); there is no
+public dataset.  The four parameter sets below are the workloads this library
+is measured and checked on:
+
+* ``SMALL``    n = 1e4,  alpha = 1.0  (gamma = 3),   kbar = 6,  seed 1
+* ``MEDIUM``   n = 1e6,  alpha = 0.75 (gamma = 2.5), kbar = 10, seed 2
+* ``LARGE``    n = 1e8,  alpha = 0.55 (gamma = 2.1), kbar = 16, seed 3
+* ``EXAMPLE``  n = 500,  alpha = 0.8, R = 5.08 -- the illustrative graph of
+  Sec. 2.1 (its R is printed, its kbar is not).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    n: int
+    alpha: float
+    kbar: float
+    seed: int
+
+
+SMALL = Workload("rhg_n1e4_a1.0_k6", 10_000, 1.0, 6.0, 1)
+MEDIUM = Workload("rhg_n1e6_a0.75_k10", 1_000_000, 0.75, 10.0, 2)
+LARGE = Workload("rhg_n1e8_a0.55_k16", 100_000_000, 0.55, 16.0, 3)
+
+ALL = (SMALL, MEDIUM, LARGE)
+
+# Sec. 2.1: "500 vertices, R ~ 5.08 and alpha = 0.8"
+EXAMPLE_N = 500
+EXAMPLE_ALPHA = 0.8
+EXAMPLE_R = 5.08
+
+
+def scaled(w: Workload, n: int, seed: int | None = None) -> Workload:
+    """Same alpha and kbar at another size (for parity at oracle-friendly n)."""
+    return Workload("%s@n%d" % (w.name, n), int(n), w.alpha, w.kbar, w.seed if seed is None else seed)
+
+
+def random_points(n: int, R: float, seed: int, r_lo: float = 0.0):
+    """Point sets for the injected-geometry entry point: r uniform on
+    [r_lo, R), phi uniform on [0, 2pi).  Not the model's radial law -- these
+    exercise the query path on arbitrary inputs."""
+    g = np.random.default_rng(seed)
+    r = g.uniform(r_lo, R, size=n)
+    phi = g.uniform(0.0, 2.0 * np.pi, size=n)
+    phi = np.where(phi >= 2.0 * np.pi, 0.0, phi)
+    return r.astype(np.float64), phi.astype(np.float64)
+
+
+def clustered_points(n: int, R: float, seed: int, clusters: int = 4, spread: float = 1e-6):
+    """Many points packed into a few tiny angular clusters near the rim:
+    stresses windows, ties in angle and wrap-around at phi = 0."""
+    g = np.random.default_rng(seed)
+    centres = g.uniform(0.0, 2.0 * np.pi, size=clusters)
+    centres[0] = 0.0  # one cluster straddles the wrap point
+    which = g.integers(0, clusters, size=n)
+    phi = np.mod(centres[which] + g.normal(0.0, spread, size=n), 2.0 * np.pi)
+    phi = np.where(phi >= 2.0 * np.pi, 0.0, phi)
+    r = R - g.exponential(1.0, size=n)
+    r = np.clip(r, 0.0, np.nextafter(R, 0.0))
+    return r.astype(np.float64), phi.astype(np.float64)

@@ -1,0 +1,416 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test ties one oracle function to an independent fact: another Philox
+implementation, mpmath at 60 digits, numerical quadrature, the paper's worked
+example, the Lemma 4 cell masses, the Poincare model of Eq. (2) and
+Proposition 1, or exhaustive high-precision enumeration.
+"""
+import math
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle as O
+from paper_1501_03545_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10: compare with Triton's Philox (run by its CPU interpreter).
+# Triton's randint4x(seed, offset) uses counter (offset, 0, 0, 0) and key
+# (seed_lo, seed_hi), the same mapping the sampler uses for vertex ids.
+# --------------------------------------------------------------------------
+_TRITON_SCRIPT = textwrap.dedent(
+    """
+    import os, sys
+    os.environ["TRITON_INTERPRET"] = "1"
+    import numpy as np, torch, triton, triton.language as tl
+
+    @triton.jit
+    def k(out_ptr, seed, base, N: tl.constexpr):
+        offs = base + tl.arange(0, N)
+        a, b, c, d = tl.randint4x(seed, offs)
+        i = tl.arange(0, N)
+        tl.store(out_ptr + i * 4 + 0, a)
+        tl.store(out_ptr + i * 4 + 1, b)
+        tl.store(out_ptr + i * 4 + 2, c)
+        tl.store(out_ptr + i * 4 + 3, d)
+
+    rows = []
+    for seed in (0, 1, 3, 0x123456789ABCDEF):
+        for base in (0, 1000, 2**31 - 64):
+            out = torch.zeros(64 * 4, dtype=torch.int32)
+            k[(1,)](out, seed, base, 64)
+            w = out.numpy().view(np.uint32).reshape(64, 4)
+            for j in range(64):
+                rows.append("%d %d %d %d %d %d" % (seed, base + j, *[int(x) for x in w[j]]))
+    sys.stdout.write("\\n".join(rows))
+    """
+)
+
+
+@pytest.fixture(scope="module")
+def triton_philox_rows():
+    pytest.importorskip("triton")
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    out = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], capture_output=True, text=True, env=env,
+                         timeout=600)
+    if out.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + out.stderr[-300:])
+    rows = []
+    for line in out.stdout.strip().splitlines():
+        s, i, a, b, c, d = (int(x) for x in line.split())
+        rows.append((s, i, (a, b, c, d)))
+    return rows
+
+
+def test_philox_matches_triton(triton_philox_rows):
+    assert len(triton_philox_rows) == 4 * 3 * 64
+    for seed, vid, words in triton_philox_rows:
+        got = O.philox([vid & 0xFFFFFFFF, vid >> 32, 0, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        assert tuple(int(x) for x in got) == words, (seed, vid)
+
+
+def test_sampler_mapping_from_independent_words(triton_philox_rows):
+    """phi = u*2pi bit-exact and r = acosh(1+u(cosh(aR)-1))/a (Eq. (1) inverse
+    CDF) within 4 ulp, with u built from Triton's Philox words."""
+    alpha, R = 0.75, 26.5
+    K = math.cosh(alpha * R) - 1.0
+    for seed in (1, 3):
+        rows = [(v, w) for s, v, w in triton_philox_rows if s == seed and v < 64]
+        r, phi = O.sample(64, alpha, R, seed)
+        for vid, (x0, x1, x2, x3) in rows:
+            up = ((x0 << 32 | x1) >> 11) * 2.0 ** -53
+            ur = ((x2 << 32 | x3) >> 11) * 2.0 ** -53
+            assert phi[vid] == up * 6.283185307179586
+            ref = np.arccosh(1.0 + ur * K) / alpha
+            assert abs(r[vid] - ref) <= 4 * np.spacing(max(ref, 1e-300))
+
+
+def test_philox_output_bits_are_balanced():
+    words = np.array([O.philox([i, 0, 0, 0], [7, 0]) for i in range(20000)], dtype=np.uint32)
+    bytes_ = words.view(np.uint8).ravel()
+    counts = np.bincount(bytes_, minlength=256)
+    chi2, p = stats.chisquare(counts)
+    assert p > 1e-4
+    bits = np.unpackbits(words.view(np.uint8)).reshape(-1, 128).mean(axis=0)
+    assert np.all(np.abs(bits - 0.5) < 0.02)
+
+
+# --------------------------------------------------------------------------
+# Eq. (22) reading and the Appendix B.1 solve.
+# --------------------------------------------------------------------------
+def _theta(r1, r2, R):
+    """Half-width of the admissible angle between radii r1 and r2 (numpy,
+    independent of the oracle's C): sin^2(t/2) = (cosh R - cosh(r1-r2)) /
+    (2 sinh r1 sinh r2); t = pi when r1 + r2 <= R."""
+    den = 2.0 * np.sinh(r1) * np.sinh(r2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        x = (np.cosh(R) - np.cosh(r1 - r2)) / den
+    x = np.where(np.isfinite(x), x, 2.0)
+    t = 2.0 * np.arcsin(np.sqrt(np.clip(x, 0.0, 1.0)))
+    return np.where(r1 + r2 <= R, np.pi, t)
+
+
+def _graded(a, b, m, nodes, w, ratio=1e-13):
+    """Gauss-Legendre nodes on [a, b], sub-intervals graded geometrically
+    toward a (where the integrand has a square-root corner)."""
+    L = b - a
+    t = np.concatenate([[0.0], np.logspace(math.log10(ratio), 0, m)])
+    xs, ws = [], []
+    for lo, hi in zip(t[:-1], t[1:]):
+        xs.append(a + L * (lo + (hi - lo) * (nodes + 1) / 2))
+        ws.append(L * (hi - lo) / 2 * w)
+    return np.concatenate(xs), np.concatenate(ws)
+
+
+def exact_mean_degree(n, alpha, R, m=48, q=16):
+    """(n-1) E[theta(r1,r2)/pi] with r1, r2 iid from Eq. (1).  Quadrature in
+    quantile space u = CDF(r); for each outer node the inner integral is 1
+    exactly up to the kink u2* = CDF(R - r1) (theta = pi there) and graded
+    Gauss-Legendre beyond it."""
+    K = math.cosh(alpha * R) - 1.0
+    nodes, w = np.polynomial.legendre.leggauss(q)
+
+    def rad(u):
+        return np.arccosh(1.0 + u * K) / alpha
+
+    u1, w1 = _graded(0.0, 1.0, m, nodes, w)
+    total = 0.0
+    for r1, wi in zip(rad(u1), w1):
+        kink = min((math.cosh(alpha * max(R - r1, 0.0)) - 1.0) / K, 1.0)
+        acc = kink
+        if kink < 1.0:
+            u2, w2 = _graded(kink, 1.0, m, nodes, w)
+            acc += np.sum(w2 * _theta(r1, rad(u2), R)) / math.pi
+        total += wi * acc
+    return (n - 1) * total
+
+
+def _eq22_literal(n, alpha, R):
+    # the garbled middle term (pi-1)*xi/alpha taken literally
+    xi = alpha / (alpha - 0.5)
+    inner = (math.pi / 4) / alpha ** 2 - (math.pi - 1) * xi / alpha + (math.pi - 2)
+    return 2 / math.pi * xi ** 2 * n * (math.exp(-R / 2) + math.exp(-alpha * R) * (alpha * R / 2 * inner - 1))
+
+
+def _read_kv(path):
+    d = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            d[k] = float(v)
+    return d
+
+
+def test_eq22_reading_on_paper_example(golden_dir):
+    ex = _read_kv(os.path.join(golden_dir, "paper_example.txt"))
+    n, alpha, R = int(ex["n"]), ex["alpha"], ex["R"]
+    ours = O.expected_degree(n, alpha, R)
+    literal = _eq22_literal(n, alpha, R)
+    exact = exact_mean_degree(n, alpha, R)
+    assert literal < 0 < ours  # the literal reading gives an impossible degree
+    assert abs(ours - exact) / exact < 0.15  # Eq. (22) is asymptotic; n = 500 is small
+    assert 100.0 < exact < 110.0
+
+
+@pytest.mark.parametrize("w", W.ALL, ids=lambda w: w.name)
+def test_eq22_matches_quadrature_at_solved_radius(w):
+    """At the workloads' sizes Eq. (22) is accurate: the exact expectation at
+    the solved R is within 0.5% of the requested degree.  A dropped term or a
+    flipped sign in the reading moves it by tens of percent."""
+    R = O.solve_radius(w.n, w.alpha, w.kbar)
+    exact = exact_mean_degree(w.n, w.alpha, R)
+    assert abs(exact - w.kbar) / w.kbar < 0.005, (R, exact)
+
+
+@pytest.mark.parametrize("w", W.ALL, ids=lambda w: w.name)
+def test_solve_radius_is_largest_double_meeting_target(w):
+    R = O.solve_radius(w.n, w.alpha, w.kbar)
+    assert O.expected_degree(w.n, w.alpha, R) >= w.kbar
+    assert O.expected_degree(w.n, w.alpha, np.nextafter(R, np.inf)) < w.kbar
+    assert O.expected_degree(w.n, w.alpha, R - 0.05) > O.expected_degree(w.n, w.alpha, R)  # decreasing branch
+
+
+def test_golden_radii_file(golden_dir):
+    for line in open(os.path.join(golden_dir, "radii.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, n, alpha, kbar, rhex, _ = line.split()
+        assert O.solve_radius(int(n), float(alpha), float(kbar)) == float.fromhex(rhex), name
+
+
+@pytest.mark.parametrize("n,alpha,kbar", [(100, 0.5, 5), (100, 0.4, 5), (100, 1.0, 0.0), (100, 1.0, 99.0),
+                                          (1, 1.0, 0.5), (100, 1.0, -1.0), (1000, 1.0, 600.0)])
+def test_solve_radius_rejects_invalid(n, alpha, kbar):
+    with pytest.raises(ValueError):
+        O.solve_radius(n, alpha, kbar)
+
+
+# --------------------------------------------------------------------------
+# Sampling: Eq. (1) and Lemma 4.
+# --------------------------------------------------------------------------
+def test_sampler_marginals_ks():
+    n, alpha = 200_000, 0.75
+    R = O.solve_radius(n, alpha, 10.0)
+    r, phi = O.sample(n, alpha, R, 11)
+    assert phi.min() >= 0.0 and phi.max() < 2 * math.pi
+    assert r.min() >= 0.0 and r.max() <= R
+    assert stats.kstest(phi / (2 * math.pi), "uniform").pvalue > 1e-3
+    F = (np.cosh(alpha * r) - 1.0) / (math.cosh(alpha * R) - 1.0)
+    assert stats.kstest(F, "uniform").pvalue > 1e-3
+
+
+def _eq3_split(lo, hi, alpha):
+    # Eq. (3): equal-probability-mass radial split of [lo, hi)
+    return math.acosh((math.cosh(alpha * hi) + math.cosh(alpha * lo)) / 2.0) / alpha
+
+
+def test_sampler_lemma4_cells_chi2():
+    """Cells of a depth-3 polar quadtree (8 angular x 8 radial with Eq. (3)
+    splits) have probability 4^-3 each by Lemma 1 / Lemma 4."""
+    n, alpha = 256_000, 0.55
+    R = O.solve_radius(10**8, alpha, 16.0)
+    r, phi = O.sample(n, alpha, R, 5)
+    edges = [0.0, R]
+    for _ in range(3):
+        new = [edges[0]]
+        for lo, hi in zip(edges[:-1], edges[1:]):
+            new += [_eq3_split(lo, hi, alpha), hi]
+        edges = new
+    ring = np.searchsorted(np.array(edges[1:-1]), r, side="right")
+    sector = np.minimum((phi / (2 * math.pi) * 8).astype(int), 7)
+    counts = np.bincount(ring * 8 + sector, minlength=64)
+    # Lemma 4 mass of each cell
+    K = math.cosh(alpha * R) - 1.0
+    mass = np.array([(math.cosh(alpha * edges[i + 1]) - math.cosh(alpha * edges[i])) / K / 8
+                     for i in range(8) for _ in range(8)])
+    assert np.allclose(mass, 1 / 64, rtol=1e-9)
+    assert stats.chisquare(counts, n * mass).pvalue > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Predicate.
+# --------------------------------------------------------------------------
+def _mp_cosh_dist(r1, p1, r2, p2):
+    import mpmath as mp
+    mp.mp.dps = 60
+    r1, p1, r2, p2 = (mp.mpf(float(x)) for x in (r1, p1, r2, p2))
+    return mp.cosh(r1) * mp.cosh(r2) - mp.sinh(r1) * mp.sinh(r2) * mp.cos(p1 - p2)
+
+
+def test_predicate_against_mpmath_at_large_radius():
+    """At R = 39 the stable form stays within a few ulp of the 60-digit
+    textbook value, including rim pairs a few 1e-9 rad apart."""
+    mp = pytest.importorskip("mpmath")
+    g = np.random.default_rng(0)
+    R = 39.029460564349
+    worst = 0.0
+    for _ in range(400):
+        r1 = R - g.exponential(1.5)
+        r2 = R - g.exponential(1.5)
+        p1 = g.uniform(0, 2 * math.pi)
+        scale = 10 ** g.uniform(-10, 0.5)
+        p2 = float(np.mod(p1 + g.choice([-1, 1]) * scale, 2 * math.pi))
+        v = O.cosh_dist(r1, p1, r2, p2)
+        ref = _mp_cosh_dist(r1, p1, r2, p2)
+        worst = max(worst, float(abs((mp.mpf(v) - ref) / ref)))
+    assert worst < 2e-14, worst
+
+
+def test_predicate_special_cases():
+    for r in (0.0, 0.3, 5.0, 20.0, 39.0):
+        assert O.cosh_dist(0.0, 1.0, r, 4.0) == math.cosh(r)  # r1 = 0: d = r2
+    for r1, r2 in ((1.0, 2.0), (10.0, 3.0), (30.0, 30.0)):
+        assert O.cosh_dist(r1, 2.0, r2, 2.0) == math.cosh(r1 - r2)  # dphi = 0: d = |r1-r2|
+        v = O.cosh_dist(r1, 0.5, r2, 0.5 + math.pi)  # dphi = pi: d = r1 + r2
+        assert abs(v - math.cosh(r1 + r2)) <= 4e-16 * math.cosh(r1 + r2)
+
+
+def test_predicate_matches_poincare_eq2_and_textbook_at_small_radius():
+    g = np.random.default_rng(1)
+    for _ in range(2000):
+        r1, r2 = g.uniform(0, 6, size=2)
+        p1, p2 = g.uniform(0, 2 * math.pi, size=2)
+        s = O.cosh_dist(r1, p1, r2, p2)
+        assert abs(O.cosh_dist_poincare(r1, p1, r2, p2) - s) <= 1e-9 * s
+        assert abs(O.cosh_dist_textbook(r1, p1, r2, p2) - s) <= 1e-9 * s
+
+
+def test_predicate_matches_proposition1_in_circle():
+    """Proposition 1's Euclidean circle is an independent edge test."""
+    g = np.random.default_rng(2)
+    R = 8.0
+    cR = math.cosh(R)
+    agree = 0
+    for _ in range(20000):
+        r1 = R * math.sqrt(g.uniform())
+        r2 = R * math.sqrt(g.uniform())
+        p1, p2 = g.uniform(0, 2 * math.pi, size=2)
+        v = O.cosh_dist(r1, p1, r2, p2)
+        if abs(v - cR) < 1e-7 * cR:
+            continue
+        assert O.in_circle_prop1(R, r1, p1, r2, p2) == (v < cR)
+        agree += 1
+    assert agree > 19000
+
+
+# --------------------------------------------------------------------------
+# Whole graph.
+# --------------------------------------------------------------------------
+def _check_csr(off, col, n):
+    assert off[0] == 0 and len(off) == n + 1 and off[-1] == len(col)
+    assert off[-1] % 2 == 0
+    rows = np.repeat(np.arange(n), np.diff(off))
+    assert np.all(col != rows)  # no self-loops
+    for i in range(n):
+        seg = col[off[i]:off[i + 1]]
+        assert np.all(np.diff(seg) > 0)  # strictly ascending
+    a = set(zip(rows.tolist(), col.tolist()))
+    assert all((j, i) in a for i, j in a)  # symmetric
+
+
+def test_brute_force_exhaustive_against_mpmath():
+    pytest.importorskip("mpmath")
+    R = 7.5
+    r, phi = W.random_points(48, R, 3)
+    r[0] = 0.0
+    off, col = O.brute_csr(r, phi, R)
+    import mpmath as mp
+    cR = mp.cosh(mp.mpf(R))
+    exp = [[] for _ in range(48)]
+    for i in range(48):
+        for j in range(48):
+            if i != j and _mp_cosh_dist(r[i], phi[i], r[j], phi[j]) < cR:
+                exp[i].append(j)
+    got = [col[off[i]:off[i + 1]].tolist() for i in range(48)]
+    assert got == exp
+    assert len(exp[0]) == 47  # the point at the centre sees every other point
+
+
+def test_brute_force_structure_small_workload():
+    w = W.SMALL
+    g = O.generate(w.n // 4, w.alpha, w.kbar, w.seed, method="brute")
+    _check_csr(g["row_off"], g["col_idx"], w.n // 4)
+
+
+@pytest.mark.parametrize("alpha,kbar", [(0.55, 16.0), (0.75, 10.0), (1.0, 6.0), (1.5, 32.0)])
+@pytest.mark.parametrize("n", [1000, 6000])
+def test_band_algorithm_equals_brute_force(n, alpha, kbar):
+    R = O.solve_radius(n, alpha, kbar)
+    r, phi = O.sample(n, alpha, R, 17 + n)
+    a = O.brute_csr(r, phi, R)
+    b = O.band_csr(r, phi, R)
+    nt, _ = O.brute_ties(r, phi, R)
+    assert nt == 0
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("kind", ["random", "clustered"])
+def test_band_algorithm_equals_brute_force_injected(kind):
+    R = 20.0
+    r, phi = (W.random_points if kind == "random" else W.clustered_points)(3000, R, 9)
+    a = O.brute_csr(r, phi, R)
+    b = O.band_csr(r, phi, R)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    ka, pa = O.brute_ties(r, phi, R)
+    kb, pb = O.Bands(r, phi, R).ties()
+    assert ka == kb and np.array_equal(np.sort(pa, axis=0), np.sort(pb, axis=0))
+
+
+def test_mean_degree_matches_exact_expectation():
+    """Measured 2m/n over 8 seeds against the quadrature expectation at the
+    solved R, 4 sigma from the seeds' own spread."""
+    n, alpha, kbar = 4000, 1.0, 6.0
+    R = O.solve_radius(n, alpha, kbar)
+    exact = exact_mean_degree(n, alpha, R)
+    means = []
+    for s in range(8):
+        r, phi = O.sample(n, alpha, R, 100 + s)
+        off, _ = O.band_csr(r, phi, R)
+        means.append(off[-1] / n)
+    m, sd = np.mean(means), np.std(means, ddof=1) / math.sqrt(len(means))
+    assert abs(m - exact) < 4 * sd + 1e-9, (m, exact, sd)
+
+
+def test_power_law_exponent_mle():
+    """Sec. 2.1: the degree tail follows a power law with exponent 2 alpha + 1.
+    Discrete MLE (Clauset-Shalizi-Newman) on the tail of a 1e6-vertex graph."""
+    n, alpha, kbar = 1_000_000, 0.75, 10.0
+    R = O.solve_radius(n, alpha, kbar)
+    r, phi = O.sample(n, alpha, R, 2)
+    b = O.Bands(r, phi, R)
+    deg = b.degrees()
+    b.close()
+    kmin = 30
+    tail = deg[deg >= kmin].astype(np.float64)
+    gamma = 1.0 + len(tail) / np.sum(np.log(tail / (kmin - 0.5)))
+    assert abs(gamma - (2 * alpha + 1)) < 0.25, gamma
+    assert abs(deg.sum() / n - kbar) / kbar < 0.05
