@@ -78,6 +78,7 @@ def lib():
             L.orc_brute_degrees.restype = _I64
             L.orc_brute_fill.argtypes = [_I64, _P, _P, _D, _P, _P]
             L.orc_brute_ties.argtypes = [_I64, _P, _P, _D, _D, _I64, _P]
+            L.orc_brute_rows.argtypes = [_I64, _P, _P, _D, _I64, _P, _P, _P, _P]
             L.orc_brute_ties.restype = _I64
             L.orc_bands_build.argtypes = [_I64, _P, _P, _D]
             L.orc_bands_build.restype = _P
@@ -178,6 +179,20 @@ def brute_csr(r, phi, R):
     col = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
     lib().orc_brute_fill(n, _ptr(r), _ptr(phi), float(R), _ptr(off), _ptr(col))
     return off, col[: int(off[-1])]
+
+
+def brute_rows(r, phi, R, qids):
+    """Sorted neighbour lists of the vertices ``qids`` by scanning all points:
+    (cnt, off, rows)."""
+    r = _f64(r)
+    phi = _f64(phi)
+    q = np.ascontiguousarray(np.asarray(qids, dtype=np.int64))
+    cnt = np.zeros(len(q), dtype=np.int64)
+    lib().orc_brute_rows(len(r), _ptr(r), _ptr(phi), float(R), len(q), _ptr(q), _ptr(cnt), None, None)
+    off = _offsets(cnt)
+    rows = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
+    lib().orc_brute_rows(len(r), _ptr(r), _ptr(phi), float(R), len(q), _ptr(q), _ptr(cnt), _ptr(off), _ptr(rows))
+    return cnt, off, rows[: int(off[-1])]
 
 
 class Bands:

@@ -251,6 +251,27 @@ void orc_brute_fill(int64_t n, const double *r, const double *phi, double R,
     }
 }
 
+/* Rows of selected vertices by scanning all n points (the definition, one
+ * row at a time, for sampled checks at sizes where all pairs are too many).
+ * First call with rows == NULL fills cnt[]; second call fills rows at off[]. */
+void orc_brute_rows(int64_t n, const double *r, const double *phi, double R, int64_t nq, const int64_t *qids,
+                    int64_t *cnt, const int64_t *off, int32_t *rows)
+{
+    double cR = cosh(R);
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < nq; ++t) {
+        int64_t i = qids[t], k = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            if (orc_cosh_dist(r[i], phi[i], r[j], phi[j]) < cR) {
+                if (rows) rows[off[t] + k] = (int32_t)j;
+                ++k;
+            }
+        }
+        if (!rows) cnt[t] = k;
+    }
+}
+
 /* Tie band: pairs i<j with |cosh d - cosh R| < tol * cosh R.  Writes up to
  * cap pairs (2 ints each) and returns how many exist. */
 int64_t orc_brute_ties(int64_t n, const double *r, const double *phi, double R, double tol,

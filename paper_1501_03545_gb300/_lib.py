@@ -1,0 +1,222 @@
+"""ctypes binding of libhrg.so (include/hrg.h).  Argument marshalling only.
+
+The functions keep the C names.  Device buffers are torch CUDA tensors (used
+for allocation and streams only); every step of the generator runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library is missing
+or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+HRG_OK, HRG_EINVAL, HRG_ENOMEM, HRG_EOVERFLOW, HRG_ECUDA, HRG_ESTATE, HRG_EINTERNAL = range(7)
+HRG_FLAG_FP64_ONLY = 0x1
+
+# every symbol declared in include/hrg.h
+EXPORTS = (
+    "hrg_solve_radius", "hrg_expected_degree", "hrg_create", "hrg_destroy", "hrg_generate_begin",
+    "hrg_generate_from_points_begin", "hrg_generate_finish", "hrg_job_stats", "hrg_job_release",
+    "hrg_generate", "hrg_generate_host", "hrg_last_error", "hrg_version",
+)
+
+
+class HrgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("hrg error %d: %s" % (code, msg))
+        self.code = code
+
+
+class hrg_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("alpha", ctypes.c_double), ("avg_degree", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("R_override", ctypes.c_double), ("flags", ctypes.c_uint32),
+                ("bands", ctypes.c_int32)]
+
+
+class hrg_stats(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double), ("n_entries", ctypes.c_int64), ("candidates", ctypes.c_uint64),
+                ("rechecks", ctypes.c_uint64), ("bands", ctypes.c_int32), ("hub_bands", ctypes.c_int32),
+                ("buckets", ctypes.c_int64), ("hub_queries", ctypes.c_int32), ("mid_rows", ctypes.c_int32),
+                ("big_rows", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mu", ctypes.c_float),
+                ("stage_ms", ctypes.c_float * 6)]
+
+    STAGES = ("sample", "bands", "count", "offsets", "write", "rowsort")
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "stage_ms")}
+        d["stage_ms"] = {s: float(self.stage_ms[i]) for i, s in enumerate(self.STAGES)}
+        return d
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def load(build_if_missing: bool = True):
+    """Loads libhrg.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.SO):
+            raise RuntimeError("libhrg.so is not built (python -m paper_1501_03545_gb300.build)")
+        L = ctypes.CDLL(_build.SO)
+        L.hrg_solve_radius.argtypes = [_I64, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+        L.hrg_expected_degree.argtypes = [_I64, ctypes.c_double, ctypes.c_double]
+        L.hrg_expected_degree.restype = ctypes.c_double
+        L.hrg_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int]
+        L.hrg_destroy.argtypes = [_P]
+        L.hrg_generate_begin.argtypes = [_P, ctypes.POINTER(hrg_params), _P, _P, _P, _P, ctypes.POINTER(_P), _PI64]
+        L.hrg_generate_from_points_begin.argtypes = [_P, _I64, ctypes.c_double, _P, _P, ctypes.c_uint32,
+                                                     ctypes.c_int32, _P, _P, ctypes.POINTER(_P), _PI64]
+        L.hrg_generate_finish.argtypes = [_P, _P]
+        L.hrg_job_stats.argtypes = [_P, ctypes.POINTER(hrg_stats)]
+        L.hrg_job_release.argtypes = [_P]
+        L.hrg_generate.argtypes = [_P, ctypes.POINTER(hrg_params), _P, _P, _P, _P, _P, _I64, _PI64,
+                                   ctypes.POINTER(hrg_stats)]
+        L.hrg_generate_host.argtypes = [_P, ctypes.POINTER(hrg_params), _P, _P, _P, _P, _I64, _PI64,
+                                        ctypes.POINTER(hrg_stats)]
+        L.hrg_last_error.argtypes = [_P]
+        L.hrg_last_error.restype = ctypes.c_char_p
+        L.hrg_version.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
+        _lib = L
+        return L
+
+
+def hrg_solve_radius(n: int, alpha: float, avg_degree: float) -> float:
+    out = ctypes.c_double()
+    rc = load().hrg_solve_radius(int(n), float(alpha), float(avg_degree), ctypes.byref(out))
+    if rc != HRG_OK:
+        raise HrgError(rc, "no radius for n=%r alpha=%r avg_degree=%r" % (n, alpha, avg_degree))
+    return out.value
+
+
+def hrg_expected_degree(n: int, alpha: float, R: float) -> float:
+    return float(load().hrg_expected_degree(int(n), float(alpha), float(R)))
+
+
+def hrg_version() -> str:
+    return load().hrg_version().decode()
+
+
+class Context:
+    """An hrg_ctx on one device (hrg_create / hrg_destroy)."""
+
+    def __init__(self, device: int = 0):
+        L = load()
+        h = _P()
+        rc = L.hrg_create(ctypes.byref(h), int(device))
+        if rc != HRG_OK:
+            raise HrgError(rc, "hrg_create(device=%d) failed" % device)
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            load().hrg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return load().hrg_last_error(self.h).decode()
+
+    def check(self, rc):
+        if rc != HRG_OK:
+            raise HrgError(rc, self.last_error())
+
+
+def params(n, alpha, avg_degree, seed, R_override=0.0, fp64_only=False, bands=0) -> hrg_params:
+    return hrg_params(int(n), float(alpha), float(avg_degree), int(seed), float(R_override),
+                      HRG_FLAG_FP64_ONLY if fp64_only else 0, int(bands))
+
+
+def _dptr(t) -> int:
+    return t.data_ptr()
+
+
+def generate(ctx: Context, n, alpha, avg_degree, seed, R_override=0.0, fp64_only=False, bands=0, stream=None):
+    """Device generation through hrg_generate_begin / hrg_generate_finish.
+    Returns dict of torch tensors (r, phi, row_off, col_idx) and stats."""
+    import torch
+
+    L = load()
+    dev = torch.device("cuda", ctx.device)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    r = torch.empty(n, dtype=torch.float64, device=dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    p = params(n, alpha, avg_degree, seed, R_override, fp64_only, bands)
+    job = _P()
+    ne = ctypes.c_int64()
+    ctx.check(L.hrg_generate_begin(ctx.h, ctypes.byref(p), _P(st.cuda_stream), _P(_dptr(r)), _P(_dptr(phi)),
+                                   _P(_dptr(off)), ctypes.byref(job), ctypes.byref(ne)))
+    try:
+        col = torch.empty(max(ne.value, 1), dtype=torch.int32, device=dev)
+        ctx.check(L.hrg_generate_finish(job, _P(_dptr(col))))
+        s = hrg_stats()
+        L.hrg_job_stats(job, ctypes.byref(s))
+    finally:
+        L.hrg_job_release(job)
+    return {"r": r, "phi": phi, "row_off": off, "col_idx": col[: ne.value], "stats": s.as_dict()}
+
+
+def generate_from_points(ctx: Context, r, phi, R, fp64_only=False, bands=0, stream=None):
+    """hrg_generate_from_points_begin + finish on caller device tensors r, phi."""
+    import torch
+
+    L = load()
+    r = r.contiguous()
+    phi = phi.contiguous()
+    n = r.numel()
+    dev = r.device
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    job = _P()
+    ne = ctypes.c_int64()
+    ctx.check(L.hrg_generate_from_points_begin(ctx.h, n, float(R), _P(_dptr(r)), _P(_dptr(phi)),
+                                               HRG_FLAG_FP64_ONLY if fp64_only else 0, int(bands),
+                                               _P(st.cuda_stream), _P(_dptr(off)), ctypes.byref(job),
+                                               ctypes.byref(ne)))
+    try:
+        col = torch.empty(max(ne.value, 1), dtype=torch.int32, device=dev)
+        ctx.check(L.hrg_generate_finish(job, _P(_dptr(col))))
+        s = hrg_stats()
+        L.hrg_job_stats(job, ctypes.byref(s))
+    finally:
+        L.hrg_job_release(job)
+    return {"row_off": off, "col_idx": col[: ne.value], "stats": s.as_dict()}
+
+
+def generate_host(ctx: Context, n, alpha, avg_degree, seed, r_host, phi_host, off_host, col_host, fp64_only=False,
+                  bands=0):
+    """hrg_generate_host into caller host tensors (pinned for full speed).
+    Returns (n_entries, stats)."""
+    L = load()
+    p = params(n, alpha, avg_degree, seed, 0.0, fp64_only, bands)
+    ne = ctypes.c_int64()
+    s = hrg_stats()
+    rc = L.hrg_generate_host(ctx.h, ctypes.byref(p), _P(r_host.data_ptr()), _P(phi_host.data_ptr()),
+                             _P(off_host.data_ptr()), _P(col_host.data_ptr()), int(col_host.numel()),
+                             ctypes.byref(ne), ctypes.byref(s))
+    ctx.check(rc)
+    return ne.value, s.as_dict()

@@ -1,0 +1,565 @@
+// hrg_api.cu -- the C ABI (include/hrg.h): contexts, jobs, workspace, plan.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hrg.h"
+#include "hrg_internal.h"
+
+using namespace hrg;
+
+// ---------------------------------------------------------------------------
+// Eq. (22) of Krioukov et al. (Appendix B.1), zeta = 1.  The expression is
+//   kbar(R) = (2/pi) xi^2 n [ e^{-R/2} + e^{-alpha R} ( (alpha R / 2) c - 1 ) ],
+//   xi = alpha / (alpha - 1/2),  c = (pi/4) alpha^-2 - (pi - 1) alpha^-1 + pi - 2.
+// ---------------------------------------------------------------------------
+static double eq22(double n, double alpha, double R)
+{
+    const double pi = 3.141592653589793;
+    const double xi = alpha / (alpha - 0.5);
+    const double ia = 1.0 / alpha;
+    const double c = (pi / 4.0) * ia * ia - (pi - 1.0) * ia + (pi - 2.0);
+    return (2.0 / pi) * xi * xi * n * (std::exp(-R / 2.0) + std::exp(-alpha * R) * (alpha * (R / 2.0) * c - 1.0));
+}
+
+extern "C" double hrg_expected_degree(int64_t n, double alpha, double R) { return eq22((double)n, alpha, R); }
+
+// The expression rises from 0 at R = 0 to one maximum and then decays; the
+// radius of a sparse graph lies on the decaying side.  Golden-section search
+// brackets the maximum, then bisection finds the largest double R with
+// kbar(R) >= target (it stops when the midpoint coincides with an end).
+extern "C" int hrg_solve_radius(int64_t n, double alpha, double avg_degree, double *R_out)
+{
+    if (!R_out || n < 2 || !(alpha > 0.5) || !(avg_degree > 0.0) || !(avg_degree < (double)(n - 1)))
+        return HRG_EINVAL;
+    const double nn = (double)n;
+    // coarse scan for the maximum on (0, 24]
+    double best = -1e300, at = 0.0;
+    for (int i = 1; i <= 2400; ++i) {
+        const double R = 0.01 * i;
+        const double k = eq22(nn, alpha, R);
+        if (k > best) { best = k; at = R; }
+    }
+    double a = std::max(0.0, at - 0.01), b = at + 0.01;
+    const double gr = 0.6180339887498949;
+    double x1 = b - gr * (b - a), x2 = a + gr * (b - a);
+    double f1 = eq22(nn, alpha, x1), f2 = eq22(nn, alpha, x2);
+    for (int it = 0; it < 120; ++it) {
+        if (f1 < f2) { a = x1; x1 = x2; f1 = f2; x2 = a + gr * (b - a); f2 = eq22(nn, alpha, x2); }
+        else { b = x2; x2 = x1; f2 = f1; x1 = b - gr * (b - a); f1 = eq22(nn, alpha, x1); }
+    }
+    const double peak = 0.5 * (a + b);
+    if (eq22(nn, alpha, peak) < avg_degree) return HRG_EINVAL;
+    double lo = peak, hi = peak + 1.0;
+    while (eq22(nn, alpha, hi) >= avg_degree) {
+        hi = peak + 2.0 * (hi - peak);
+        if (hi > 1e7) return HRG_EINVAL;
+    }
+    for (;;) {
+        const double mid = lo + 0.5 * (hi - lo);
+        if (!(mid > lo && mid < hi)) break;
+        if (eq22(nn, alpha, mid) >= avg_degree) lo = mid; else hi = mid;
+    }
+    *R_out = lo;
+    return HRG_OK;
+}
+
+extern "C" const char *hrg_version(void) { return "hrg-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// Context and workspace.
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct hrg_job {
+    hrg_ctx *ctx = nullptr;
+    Plan plan{};
+    bool fp64 = false;
+    bool open = false;
+    bool finished = false;
+    int32_t p_hub = 0;
+    int n_mid = 0, n_big = 0;
+    int64_t big_total = 0;
+    int64_t n_entries = 0;
+    uint64_t stats[8] = {};
+    float stage_ms[6] = {};
+    const double *r = nullptr, *phi = nullptr;
+    int64_t *row_off = nullptr;
+    cudaStream_t stream = nullptr;
+    QueryBufs qb{};
+};
+
+struct hrg_ctx {
+    int device = 0;
+    std::string err;
+    // workspace slots
+    enum { W_BANDCNT, W_GBUF, W_CNT, W_START, W_PERM, W_A, W_PMS, W_PMS64, W_DEG, W_STATS, W_MID, W_BIG,
+           W_LISTCNT, W_BIGTOT, W_SCAN, W_TMP, W_BUCKET, W_OUT_R, W_OUT_PHI, W_OUT_OFF, W_OUT_COL, W_COUNT };
+    DevBuf ws[W_COUNT];
+    void *pinned = nullptr;  // small pinned staging area for read-backs
+    cudaEvent_t ev[8] = {};  // stage boundaries of the current job
+    hrg_job job;
+};
+
+static int set_err(hrg_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return set_err(ctx, HRG_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                           __FILE__, __LINE__);                                                    \
+    } while (0)
+
+static int ensure(hrg_ctx *ctx, int slot, size_t bytes, void **out)
+{
+    DevBuf &b = ctx->ws[slot];
+    if (bytes == 0) bytes = 16;
+    if (b.bytes < bytes) {
+        if (b.ptr) cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+        const size_t want = bytes + bytes / 8;  // grow with some slack
+        cudaError_t e = cudaMalloc(&b.ptr, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            e = cudaMalloc(&b.ptr, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                b.ptr = nullptr;
+                return set_err(ctx, HRG_ENOMEM, "device allocation of %zu bytes failed", bytes);
+            }
+            b.bytes = bytes;
+        } else {
+            b.bytes = want;
+        }
+    }
+    *out = b.ptr;
+    return HRG_OK;
+}
+
+extern "C" int hrg_create(hrg_ctx **out, int device)
+{
+    if (!out) return HRG_EINVAL;
+    *out = nullptr;
+    hrg_ctx *ctx = new hrg_ctx();
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return HRG_ECUDA;
+    }
+    e = cudaMallocHost(&ctx->pinned, 4096);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return HRG_ENOMEM;
+    }
+    for (auto &ev : ctx->ev) {
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+            cudaFreeHost(ctx->pinned);
+            delete ctx;
+            return HRG_ECUDA;
+        }
+    }
+    *out = ctx;
+    return HRG_OK;
+}
+
+extern "C" int hrg_destroy(hrg_ctx *ctx)
+{
+    if (!ctx) return HRG_EINVAL;
+    cudaSetDevice(ctx->device);
+    for (auto &b : ctx->ws)
+        if (b.ptr) cudaFree(b.ptr);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    for (auto &ev : ctx->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete ctx;
+    return HRG_OK;
+}
+
+extern "C" const char *hrg_last_error(const hrg_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// Plan.
+// ---------------------------------------------------------------------------
+static float f32(double x) { return (float)x; }
+
+// Band layout before the band counts are known.
+static void plan_bands(Plan &p, int64_t n, double R, double alpha, int bands)
+{
+    memset(&p, 0, sizeof p);
+    p.n = n;
+    p.R = R;
+    p.coshR = std::cosh(R);
+    p.alpha = alpha;
+    p.big = std::cosh(alpha * R) - 1.0;
+    p.half_R = 0.5 * R;
+    int B = bands > 0 ? bands : (int)std::ceil(R / 1.25);
+    if (B < 1) B = 1;
+    if (B > HRG_MAX_BANDS) B = HRG_MAX_BANDS;
+    p.B = B;
+    p.inv_width = (double)B / R;
+    for (int k = 0; k < B; ++k) p.band_lo[k] = R * (double)k / (double)B;
+    p.band_lo[B] = INFINITY;
+    for (int k = 0; k < B; ++k) {
+        const double b = p.band_lo[k];
+        p.Pb[k] = f32(std::exp(b - 0.5 * R));
+        p.Mb[k] = f32(std::exp(-b - 0.5 * R));
+        p.Sb[k] = f32(2.0 * std::exp(-0.5 * R) * std::sinh(b));
+    }
+    p.rhs64 = 1.0 + std::exp(-2.0 * R);
+    p.rhs32 = f32(p.rhs64);
+    // Undecided band of the FP32 filter: the FP32 value carries a relative
+    // error below ~2^-19 from its inputs and operations, plus the difference
+    // between the fixed-point angle and the FP64 angles (<= ~2e-15 rad
+    // absolute), which near the threshold (|dphi| >= ~2 e^{-R/2}) is a relative
+    // error of at most ~1e-15 e^{R/2} on sin(dphi/2).
+    p.mu = f32(2e-4 + 8e-15 * std::exp(0.5 * R));
+}
+
+// Angular buckets and hub bands once the band counts are known.
+static void plan_buckets(Plan &p, const int64_t *cnt, int32_t *p_hub)
+{
+    int64_t G = 0;
+    for (int k = 0; k < p.B; ++k) {
+        int g = 0;
+        while (g < 40 && ((int64_t)1 << (g + 1)) <= cnt[k]) ++g;
+        p.gbits[k] = g;
+        p.base[k] = G;
+        G += (int64_t)1 << g;
+    }
+    p.base[p.B] = G;
+    p.G = G;
+    // hub bands: expected candidates of a query at the band's inner radius
+    // above ~2048 (sum over bands of count * window / pi)
+    int hub = 0;
+    for (int i = 0; i < p.B; ++i) {
+        const double rq = p.band_lo[i];
+        double cand = 0.0;
+        for (int j = 0; j < p.B; ++j) {
+            const double b = p.band_lo[j];
+            double frac;
+            if (rq + b <= p.R || rq == 0.0 || b == 0.0) frac = 1.0;
+            else {
+                double x = (p.coshR - std::cosh(rq - b)) / (2.0 * std::sinh(rq) * std::sinh(b));
+                x = std::min(1.0, std::max(0.0, x));
+                frac = 2.0 * std::asin(std::sqrt(x)) / 3.141592653589793;
+            }
+            cand += frac * (double)cnt[j];
+        }
+        if (cand > 2048.0) hub = i + 1; else break;
+    }
+    p.hub_bands = hub;
+    int64_t ph = 0;
+    for (int k = 0; k < hub; ++k) ph += cnt[k];
+    *p_hub = (int32_t)ph;
+}
+
+static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params *prm, int64_t n, double R,
+                        double alpha, const double *r_in, const double *phi_in, double *r_out, double *phi_out,
+                        uint32_t flags, int32_t bands, cudaStream_t st, int64_t *row_off_out, int64_t *n_entries)
+{
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    J = hrg_job();
+    J.ctx = ctx;
+    J.stream = st;
+    J.fp64 = (flags & HRG_FLAG_FP64_ONLY) != 0 || R > 80.0;
+    J.row_off = row_off_out;
+    Plan &p = J.plan;
+    plan_bands(p, n, R, alpha, bands);
+
+    void *band_cnt, *gbuf, *perm, *A, *pms, *pms64 = nullptr, *deg, *stats, *mid, *big, *listcnt, *bigtot, *scanws;
+    int rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_BANDCNT, sizeof(int64_t) * HRG_MAX_BANDS, &band_cnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_GBUF, sizeof(int32_t) * n, &gbuf))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_PERM, sizeof(int32_t) * n, &perm))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_A, sizeof(uint64_t) * n, &A))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_PMS, sizeof(PMS) * n, &pms))) return rc;
+    if (J.fp64 && (rc = ensure(ctx, hrg_ctx::W_PMS64, sizeof(PMS64) * n, &pms64))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_DEG, sizeof(int32_t) * n, &deg))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_STATS, sizeof(uint64_t) * 8, &stats))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_MID, sizeof(int32_t) * n, &mid))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_BIG, sizeof(int32_t) * n, &big))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 2, &listcnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_BIGTOT, sizeof(int64_t), &bigtot))) return rc;
+
+    // 1. points and band counts
+    CK(cudaEventRecord(ctx->ev[0], st));
+    CK(cudaMemsetAsync(band_cnt, 0, sizeof(int64_t) * HRG_MAX_BANDS, st));
+    if (sampled) {
+        CK(launch_sample(p, prm->seed, r_out, phi_out, (int64_t *)band_cnt, st));
+        J.r = r_out;
+        J.phi = phi_out;
+    } else {
+        CK(launch_count_bands(p, r_in, phi_in, (int64_t *)band_cnt, st));
+        J.r = r_in;
+        J.phi = phi_in;
+    }
+    CK(cudaEventRecord(ctx->ev[1], st));
+    int64_t *h_cnt = (int64_t *)ctx->pinned;
+    CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int64_t cnt_copy[HRG_MAX_BANDS];
+    memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
+    plan_buckets(p, cnt_copy, &J.p_hub);
+
+    // 2. counting sort by (band, angular bucket)
+    void *cnt, *start;
+    const size_t scan_bytes = std::max(scan_workspace_bytes(p.G), scan_workspace_bytes(n));
+    if ((rc = ensure(ctx, hrg_ctx::W_CNT, sizeof(int32_t) * p.G, &cnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_START, sizeof(int32_t) * (p.G + 1), &start))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_bytes, &scanws))) return rc;
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * p.G, st));
+    CK(launch_bucket_hist(p, J.r, J.phi, (int32_t *)gbuf, (int32_t *)cnt, st));
+    CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, p.G, scanws, st));
+    CK(launch_bucket_scatter(p, (int32_t *)gbuf, (int32_t *)start, (int32_t *)cnt, (int32_t *)perm, st));
+    CK(launch_build_soa(p, (int32_t *)perm, J.r, J.phi, (uint64_t *)A, (PMS *)pms, (PMS64 *)pms64, st));
+    CK(cudaEventRecord(ctx->ev[2], st));
+
+    // 3. degrees
+    QueryBufs &b = J.qb;
+    b.A = (uint64_t *)A;
+    b.pms = (PMS *)pms;
+    b.pms64 = (PMS64 *)pms64;
+    b.start = (int32_t *)start;
+    b.r = J.r;
+    b.phi = J.phi;
+    b.deg = (int32_t *)deg;
+    b.stats = (unsigned long long *)stats;
+    b.mid_rows = (int32_t *)mid;
+    b.big_rows = (int32_t *)big;
+    b.list_cnt = (int32_t *)listcnt;
+    b.big_total = (int64_t *)bigtot;
+    CK(cudaMemsetAsync(stats, 0, sizeof(uint64_t) * 8, st));
+    CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 2, st));
+    CK(cudaMemsetAsync(bigtot, 0, sizeof(int64_t), st));
+    CK(launch_count_split(p, b, J.fp64, J.p_hub, st));
+    CK(cudaEventRecord(ctx->ev[3], st));
+
+    // 4. row offsets
+    CK(scan_i32_to_i64((int32_t *)deg, row_off_out, n, scanws, st));
+    CK(cudaEventRecord(ctx->ev[4], st));
+    char *hp = (char *)ctx->pinned;
+    CK(cudaMemcpyAsync(hp + 0, row_off_out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 8, listcnt, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 16, bigtot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 64, stats, sizeof(uint64_t) * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    memcpy(&J.n_entries, hp + 0, 8);
+    int32_t lc[2];
+    memcpy(lc, hp + 8, 8);
+    J.n_mid = lc[0];
+    J.n_big = lc[1];
+    memcpy(&J.big_total, hp + 16, 8);
+    memcpy(J.stats, hp + 64, 64);
+    J.open = true;
+    *n_entries = J.n_entries;
+    return HRG_OK;
+}
+
+static int check_params(hrg_ctx *ctx, const hrg_params *p, double *R)
+{
+    if (!p) return set_err(ctx, HRG_EINVAL, "null params");
+    if (p->n < 2 || p->n > 0x7fffffffLL) return set_err(ctx, HRG_EINVAL, "n must be in [2, 2^31)");
+    if (!(p->alpha > 0.5)) return set_err(ctx, HRG_EINVAL, "alpha must exceed 1/2");
+    if (p->bands < 0 || p->bands > HRG_MAX_BANDS) return set_err(ctx, HRG_EINVAL, "bands must be in [0, 64]");
+    if (p->R_override > 0.0) {
+        *R = p->R_override;
+        return HRG_OK;
+    }
+    if (hrg_solve_radius(p->n, p->alpha, p->avg_degree, R) != HRG_OK)
+        return set_err(ctx, HRG_EINVAL, "no radius for n=%lld alpha=%g avg_degree=%g (Eq. (22))",
+                       (long long)p->n, p->alpha, p->avg_degree);
+    return HRG_OK;
+}
+
+extern "C" int hrg_generate_begin(hrg_ctx *ctx, const hrg_params *p, void *stream, double *r_out, double *phi_out,
+                                  int64_t *row_off_out, hrg_job **job, int64_t *n_entries)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (!job || !n_entries || !r_out || !phi_out || !row_off_out) return set_err(ctx, HRG_EINVAL, "null argument");
+    if (ctx->job.open) return set_err(ctx, HRG_ESTATE, "a job of this context is still open");
+    double R;
+    int rc = check_params(ctx, p, &R);
+    if (rc) return rc;
+    rc = begin_common(ctx, ctx->job, true, p, p->n, R, p->alpha, nullptr, nullptr, r_out, phi_out, p->flags,
+                      p->bands, (cudaStream_t)stream, row_off_out, n_entries);
+    if (rc) {
+        ctx->job.open = false;
+        return rc;
+    }
+    *job = &ctx->job;
+    return HRG_OK;
+}
+
+extern "C" int hrg_generate_from_points_begin(hrg_ctx *ctx, int64_t n, double R, const double *r, const double *phi,
+                                              uint32_t flags, int32_t bands, void *stream, int64_t *row_off_out,
+                                              hrg_job **job, int64_t *n_entries)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (!job || !n_entries || !r || !phi || !row_off_out) return set_err(ctx, HRG_EINVAL, "null argument");
+    if (ctx->job.open) return set_err(ctx, HRG_ESTATE, "a job of this context is still open");
+    if (n < 1 || n > 0x7fffffffLL) return set_err(ctx, HRG_EINVAL, "n must be in [1, 2^31)");
+    if (!(R > 0.0) || !std::isfinite(R)) return set_err(ctx, HRG_EINVAL, "R must be positive and finite");
+    if (bands < 0 || bands > HRG_MAX_BANDS) return set_err(ctx, HRG_EINVAL, "bands must be in [0, 64]");
+    int rc = begin_common(ctx, ctx->job, false, nullptr, n, R, 1.0, r, phi, nullptr, nullptr, flags, bands,
+                          (cudaStream_t)stream, row_off_out, n_entries);
+    if (rc) {
+        ctx->job.open = false;
+        return rc;
+    }
+    *job = &ctx->job;
+    return HRG_OK;
+}
+
+extern "C" int hrg_generate_finish(hrg_job *job, int32_t *col_idx_out)
+{
+    if (!job || !job->ctx) return HRG_EINVAL;
+    hrg_ctx *ctx = job->ctx;
+    if (!job->open || job->finished) return set_err(ctx, HRG_ESTATE, "job is not open");
+    if (!col_idx_out && job->n_entries > 0) return set_err(ctx, HRG_EINVAL, "null col_idx");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    cudaStream_t st = job->stream;
+    const Plan &p = job->plan;
+    CK(cudaEventRecord(ctx->ev[5], st));
+    CK(launch_write_split(p, job->qb, job->fp64, job->p_hub, job->row_off, col_idx_out, st));
+    CK(cudaEventRecord(ctx->ev[6], st));
+    if (job->n_mid > 0 || job->n_big > 0) {
+        void *tmp = nullptr, *bws = nullptr;
+        int rc;
+        int64_t bws_words = 16;
+        if (job->n_big > 0) {
+            if ((rc = ensure(ctx, hrg_ctx::W_TMP, sizeof(int32_t) * job->big_total, &tmp))) return rc;
+            bws_words = (int64_t)(((size_t)job->n_big * 16 + 3) / 4 + big_sort_hist_words(p.n, job->n_big));
+        }
+        if ((rc = ensure(ctx, hrg_ctx::W_BUCKET, sizeof(int32_t) * bws_words, &bws))) return rc;
+        CK(launch_sort_rows(p, job->qb, job->n_mid, job->n_big, job->row_off, col_idx_out, (int32_t *)tmp,
+                            job->big_total, (int32_t *)bws, bws_words, st));
+    }
+    CK(cudaEventRecord(ctx->ev[7], st));
+    uint64_t *hs = (uint64_t *)ctx->pinned;
+    CK(cudaMemcpyAsync(hs, job->qb.stats + 7, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    job->finished = true;
+    const int pairs[6][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {5, 6}, {6, 7}};
+    for (int k = 0; k < 6; ++k) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[pairs[k][0]], ctx->ev[pairs[k][1]]) != cudaSuccess) {
+            cudaGetLastError();
+            ms = -1.0f;
+        }
+        job->stage_ms[k] = ms;
+    }
+    if (hs[0] != 0) return set_err(ctx, HRG_EINTERNAL, "count and write passes disagree on a row");
+    return HRG_OK;
+}
+
+extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
+{
+    if (!job || !out) return HRG_EINVAL;
+    memset(out, 0, sizeof *out);
+    out->R = job->plan.R;
+    out->n_entries = job->n_entries;
+    out->candidates = job->stats[0];
+    out->rechecks = job->stats[1];
+    out->bands = job->plan.B;
+    out->hub_bands = job->plan.hub_bands;
+    out->buckets = job->plan.G;
+    out->hub_queries = job->p_hub;
+    out->mid_rows = job->n_mid;
+    out->big_rows = job->n_big;
+    out->mu = job->plan.mu;
+    for (int k = 0; k < 6; ++k) out->stage_ms[k] = job->stage_ms[k];
+    return HRG_OK;
+}
+
+extern "C" int hrg_job_release(hrg_job *job)
+{
+    if (!job || !job->ctx) return HRG_EINVAL;
+    job->open = false;
+    job->finished = false;
+    return HRG_OK;
+}
+
+extern "C" int hrg_generate(hrg_ctx *ctx, const hrg_params *p, void *stream, double *r_out, double *phi_out,
+                            int64_t *row_off_out, int32_t *col_idx_out, int64_t col_capacity, int64_t *n_entries,
+                            hrg_stats *stats_out)
+{
+    hrg_job *job = nullptr;
+    int64_t ne = 0;
+    int rc = hrg_generate_begin(ctx, p, stream, r_out, phi_out, row_off_out, &job, &ne);
+    if (rc) return rc;
+    if (n_entries) *n_entries = ne;
+    if (ne > col_capacity) {
+        if (stats_out) hrg_job_stats(job, stats_out);
+        hrg_job_release(job);
+        return set_err(ctx, HRG_EOVERFLOW, "graph has %lld entries, capacity %lld", (long long)ne,
+                       (long long)col_capacity);
+    }
+    rc = hrg_generate_finish(job, col_idx_out);
+    if (stats_out) hrg_job_stats(job, stats_out);
+    hrg_job_release(job);
+    return rc;
+}
+
+extern "C" int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_host, double *phi_host,
+                                 int64_t *row_off_host, int32_t *col_idx_host, int64_t col_capacity,
+                                 int64_t *n_entries, hrg_stats *stats_out)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (!p || !r_host || !phi_host || !row_off_host || !n_entries) return set_err(ctx, HRG_EINVAL, "null argument");
+    if (p->n < 2 || p->n > 0x7fffffffLL) return set_err(ctx, HRG_EINVAL, "n must be in [2, 2^31)");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    const int64_t n = p->n;
+    void *dr, *dphi, *doff, *dcol;
+    int rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_OUT_R, sizeof(double) * n, &dr))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_OUT_PHI, sizeof(double) * n, &dphi))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_OUT_OFF, sizeof(int64_t) * (n + 1), &doff))) return rc;
+    hrg_job *job = nullptr;
+    int64_t ne = 0;
+    cudaStream_t st = nullptr;
+    rc = hrg_generate_begin(ctx, p, st, (double *)dr, (double *)dphi, (int64_t *)doff, &job, &ne);
+    if (rc) return rc;
+    *n_entries = ne;
+    if (ne > col_capacity || (ne > 0 && !col_idx_host)) {
+        if (stats_out) hrg_job_stats(job, stats_out);
+        hrg_job_release(job);
+        return set_err(ctx, HRG_EOVERFLOW, "graph has %lld entries, capacity %lld", (long long)ne,
+                       (long long)col_capacity);
+    }
+    if ((rc = ensure(ctx, hrg_ctx::W_OUT_COL, sizeof(int32_t) * (ne > 0 ? ne : 1), &dcol))) {
+        hrg_job_release(job);
+        return rc;
+    }
+    rc = hrg_generate_finish(job, (int32_t *)dcol);
+    if (stats_out) hrg_job_stats(job, stats_out);
+    hrg_job_release(job);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(r_host, dr, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(phi_host, dphi, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(row_off_host, doff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+    if (ne > 0) CK(cudaMemcpyAsync(col_idx_host, dcol, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return HRG_OK;
+}

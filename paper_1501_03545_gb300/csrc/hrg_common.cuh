@@ -1,0 +1,230 @@
+// hrg_common.cuh -- device-side building blocks of the RHG generator.
+//
+// Shared by the generator's translation units only (never by the CPU oracle).
+// Notation follows von Looz et al., "Fast generation of complex networks with
+// underlying hyperbolic geometry": n points on the hyperbolic disk of radius
+// R (curvature -1), angle phi uniform on [0, 2pi), radius r with density
+// alpha sinh(alpha r) / (cosh(alpha R) - 1) (Eq. (1)); u ~ v iff
+// dist(u, v) < R (Sec. 2.1).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define HRG_MAX_BANDS 64
+
+namespace hrg {
+
+// ---------------------------------------------------------------------------
+// Plan: everything a kernel needs to know about one graph.  Filled on the
+// host (hrg_api.cu) and passed by value.
+// ---------------------------------------------------------------------------
+struct Plan {
+    int64_t n;
+    double R, coshR, alpha;
+    double big;          // cosh(alpha R) - 1, the scale of Eq. (1)'s inverse CDF
+    double half_R;       // R / 2
+    double inv_width;    // B / R
+    int B;               // number of radial bands
+    int hub_bands;       // bands [0, hub_bands) are queried by whole CTAs
+    int64_t G;           // total number of angular buckets over all bands
+    double band_lo[HRG_MAX_BANDS + 1];  // inner radius of each band; band_lo[B] = +inf
+    int64_t base[HRG_MAX_BANDS + 1];    // first bucket of each band; base[B] = G
+    int gbits[HRG_MAX_BANDS];           // log2(#buckets) of each band
+    float Pb[HRG_MAX_BANDS], Mb[HRG_MAX_BANDS], Sb[HRG_MAX_BANDS];  // scaled exps at band_lo
+    float rhs32;         // 1 + e^{-2R} rounded to float
+    float mu;            // half-width of the FP32 filter's undecided band (relative)
+    double rhs64;        // 1 + e^{-2R}
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The counter block is
+// (id_lo, id_hi, 0, 0) and the key (seed_lo, seed_hi); ten rounds, each a
+// pair of 32x32->64 multiplications with the halves swapped and xored with
+// the key, the key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox_block(uint64_t ctr, uint64_t seed)
+{
+    const uint32_t MUL_A = 0xD2511F53u, MUL_B = 0xCD9E8D57u;
+    const uint32_t BUMP_A = 0x9E3779B9u, BUMP_B = 0xBB67AE85u;
+    U4 s{(uint32_t)ctr, (uint32_t)(ctr >> 32), 0u, 0u};
+    uint32_t ka = (uint32_t)seed, kb = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t ha = __umulhi(MUL_A, s.x), la = MUL_A * s.x;
+        const uint32_t hb = __umulhi(MUL_B, s.z), lb = MUL_B * s.z;
+        s = U4{hb ^ s.y ^ ka, lb, ha ^ s.w ^ kb, la};
+        ka += BUMP_A;
+        kb += BUMP_B;
+    }
+    return s;
+}
+
+// the uniform on [0,1) made of the top 53 bits of a 64-bit word
+__device__ __forceinline__ double unit53(uint32_t hi, uint32_t lo)
+{
+    const uint64_t w = ((uint64_t)hi << 32) | (uint64_t)lo;
+    return (double)(w >> 11) * 0x1.0p-53;
+}
+
+constexpr double kTwoPi = 6.283185307179586;          // the double nearest 2 pi
+constexpr double kAngleScale = 2.9358905032820014e18;  // 2^64 / (2 pi): angle -> 64-bit fixed point
+constexpr float kAngleScaleUp = 2.9358906e18f;         // the same, rounded up (windows stay conservative)
+constexpr float kAngleUnit = 3.4061215800865545e-19f;  // 2 pi / 2^64
+
+// Fixed-point angle A in [0, 2^64) for phi in [0, 2pi): monotone in phi, and
+// within 2^12 units of phi * 2^64 / (2 pi).  Differences of A taken as signed
+// 64-bit integers are circular angle differences.
+__device__ __forceinline__ uint64_t angle_key(double phi)
+{
+    double a = __dmul_rn(phi, kAngleScale);
+    if (!(a > 0.0)) return 0ull;
+    if (a >= 18446744073709551615.0) return 0xFFFFFFFFFFFFFFFFull;
+    return __double2ull_rz(a);
+}
+
+// radial band: the k with band_lo[k] <= r < band_lo[k+1]
+__device__ __forceinline__ int band_of(const Plan &p, double r)
+{
+    int k = (int)(r * p.inv_width);
+    if (k < 0) k = 0;
+    if (k > p.B - 1) k = p.B - 1;
+    while (k > 0 && r < p.band_lo[k]) --k;
+    while (k < p.B - 1 && r >= p.band_lo[k + 1]) ++k;
+    return k;
+}
+
+__device__ __forceinline__ int64_t bucket_of(const Plan &p, int band, uint64_t A)
+{
+    const int g = p.gbits[band];
+    return p.base[band] + (g == 0 ? 0 : (int64_t)(A >> (64 - g)));
+}
+
+// ---------------------------------------------------------------------------
+// Scaled exponentials.  With P = e^{r - R/2}, M = e^{-r - R/2} and
+// S = P - M = 2 e^{-R/2} sinh r, the edge rule of Sec. 2.1 in the form
+//   cosh(r1 - r2) + 2 sinh r1 sinh r2 sin^2(dphi/2) < cosh R
+// multiplied by 2 e^{-R} reads
+//   P1 M2 + P2 M1 + S1 S2 sin^2(dphi/2) < 1 + e^{-2R},
+// all terms non-negative and bounded by e^{R} for r <= R.
+// ---------------------------------------------------------------------------
+struct __align__(16) PMS { float P, M, S; int32_t id; };
+
+__device__ __forceinline__ float exp_split(double t)
+{
+    // e^t in float with the argument kept to ~2^-48 relative: t = hi + lo
+    const float hi = (float)t;
+    const float lo = (float)(t - (double)hi);
+    return expf(hi) * (1.0f + lo);
+}
+
+__device__ __forceinline__ PMS scaled_exps(const Plan &p, double r, int32_t id)
+{
+    PMS o;
+    const double t = r - p.half_R;
+    o.P = exp_split(t);
+    o.M = exp_split(-t - p.R);
+    // S = P (1 - e^{-2r}); expm1f keeps small radii accurate
+    o.S = o.P * (-expm1f(-2.0f * (float)r));
+    o.id = id;
+    return o;
+}
+
+// sin(x) for |x| <= pi/2 by its Taylor series through x^11 (Horner in x^2);
+// truncation error <= (pi/2)^13/13! < 6e-8 at the interval's end.
+__device__ __forceinline__ float sin_taylor(float x)
+{
+    const float t = x * x;
+    float s = -2.5052108e-8f;           // -1/11!
+    s = fmaf(s, t, 2.7557319e-6f);      //  1/9!
+    s = fmaf(s, t, -1.9841270e-4f);     // -1/7!
+    s = fmaf(s, t, 8.3333333e-3f);      //  1/5!
+    s = fmaf(s, t, -1.6666667e-1f);     // -1/3!
+    s = fmaf(s, t, 1.0f);
+    return x * s;
+}
+
+// FP32 value of P1 M2 + P2 M1 + S1 S2 sin^2(dA/2) for a fixed-point angle
+// difference dA (signed, |dA| <= 2^63 <-> pi).
+__device__ __forceinline__ float lhs32(const PMS &q, const PMS &c, int64_t dA)
+{
+    const float half = __ll2float_rn(dA) * (0.5f * kAngleUnit);
+    const float s = sin_taylor(half);
+    return fmaf(q.S * c.S, s * s, fmaf(q.P, c.M, c.P * q.M));
+}
+
+// sin(x) for |x| <= 2^-4 by Taylor through x^9 (error < x^11/11! < 1e-20 |x|),
+// the CUDA library sin beyond.
+__device__ __forceinline__ double sin_small64(double x)
+{
+    if (fabs(x) > 0.0625) return sin(x);
+    const double t = x * x;
+    double s = 2.7557319223985893e-6;            //  1/9!
+    s = fma(s, t, -1.9841269841269841e-4);       // -1/7!
+    s = fma(s, t, 8.3333333333333333e-3);        //  1/5!
+    s = fma(s, t, -1.6666666666666667e-1);       // -1/3!
+    s = fma(s, t, 1.0);
+    return x * s;
+}
+
+// Exact FP64 decision from the stored coordinates (the recheck, and the
+// reference form of the predicate): cosh(r1-r2) + 2 sinh r1 sinh r2 s^2 < cosh R
+// with s = sin((phi1 - phi2)/2) computed from the same doubles the caller
+// sees.  Relative error a few ulp, far inside the 1e-12 tie band.
+__device__ __forceinline__ bool edge64(double r1, double phi1, double r2, double phi2, double coshR)
+{
+    const double s = sin_small64(0.5 * (phi1 - phi2));
+    const double v = cosh(r1 - r2) + 2.0 * sinh(r1) * sinh(r2) * (s * s);
+    return v < coshR;
+}
+
+// FP64 per-point data of the plain double-precision path
+struct __align__(16) PMS64 { double P, M, S, phi; };
+
+__device__ __forceinline__ PMS64 scaled_exps64(const Plan &p, double r, double phi)
+{
+    PMS64 o;
+    o.P = exp(r - p.half_R);
+    o.M = exp(-r - p.half_R);
+    o.S = 2.0 * exp(-p.half_R) * sinh(r);
+    o.phi = phi;
+    return o;
+}
+
+__device__ __forceinline__ bool edge_pms64(const Plan &p, const PMS64 &q, const PMS64 &c)
+{
+    const double s = sin_small64(0.5 * (q.phi - c.phi));
+    const double v = fma(q.S * c.S, s * s, fma(q.P, c.M, c.P * q.M));
+    return v < p.rhs64;
+}
+
+// ---------------------------------------------------------------------------
+// Angular window of a query in a band (replaces Proposition 1 + the range
+// query of Algorithm 1).  For r_c >= b the admissible |dphi| is at most
+// theta(r_q, b) with sin^2(theta/2) = (cosh R - cosh(r_q - b)) /
+// (2 sinh r_q sinh b) = (1 + e^{-2R} - P_q M_b - P_b M_q) / (S_q S_b).
+// Computed in FP32 and padded so that it never excludes a neighbour; returns
+// the half-width in fixed-point angle units, or ~0 (all ones) for the whole
+// circle.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kFullCircle = 0xFFFFFFFFFFFFFFFFull;
+
+__device__ __forceinline__ uint64_t window_halfwidth(const Plan &p, const PMS &q, int band)
+{
+    const float Pb = p.Pb[band], Mb = p.Mb[band], Sb = p.Sb[band];
+    const float den = q.S * Sb;
+    if (!(den > 0.0f)) return kFullCircle;
+    const float sub = fmaf(q.P, Mb, Pb * q.M);
+    const float num = p.rhs32 - sub;
+    float X = num / den;
+    X = X * (1.0f + 2e-5f) + 2e-5f * (1.0f + sub) / den;
+    if (X >= 1.0f) return kFullCircle;
+    if (!(X > 0.0f)) X = 0.0f;
+    float th = 2.0f * asinf(sqrtf(X));
+    th = th * (1.0f + 2e-5f) + 1e-30f;
+    if (th >= 3.1415f) return kFullCircle;
+    return __float2ull_ru(th * kAngleScaleUp) + (1ull << 16);
+}
+
+}  // namespace hrg

@@ -1,0 +1,259 @@
+// hrg_points.cu -- point sampling and the angle-sorted radial-band structure.
+//
+// Algorithm 1 draws every point, maps it to the Poincare disk and inserts it
+// into a polar quadtree.  Here the points stay in native coordinates and the
+// quadtree is replaced by B radial bands, each cut into 2^g equal angular
+// buckets (g chosen so a bucket holds about one point).  A counting sort by
+// (band, bucket) gives every band as a contiguous, angle-bucketed array; the
+// bucket start table doubles as the angular index used by the queries.
+#include <cstdio>
+#include "hrg_internal.h"
+
+namespace hrg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t n, int threads, int per_thread = 1)
+{
+    int64_t g = (n + (int64_t)threads * per_thread - 1) / ((int64_t)threads * per_thread);
+    if (g < 1) g = 1;
+    if (g > (1 << 20)) g = 1 << 20;
+    return (int)g;
+}
+
+// per-band counts: shared-memory histogram, one global atomic per band per block
+__device__ __forceinline__ void band_hist_flush(const Plan &p, int *sh, int64_t *band_cnt)
+{
+    __syncthreads();
+    for (int k = threadIdx.x; k < p.B; k += blockDim.x)
+        if (sh[k]) atomicAdd((unsigned long long *)&band_cnt[k], (unsigned long long)sh[k]);
+}
+
+// Algorithm 1's two draws: phi uniform on [0, 2pi) and r with density
+// Eq. (1), by the inverse CDF r = acosh(1 + u (cosh(alpha R) - 1)) / alpha.
+// Uniforms come from Philox4x32-10 at counter = vertex id, key = seed.
+__global__ void k_sample(Plan p, uint64_t seed, double *__restrict__ r_out, double *__restrict__ phi_out,
+                         int64_t *__restrict__ band_cnt)
+{
+    __shared__ int sh[HRG_MAX_BANDS];
+    for (int k = threadIdx.x; k < HRG_MAX_BANDS; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+        const U4 w = philox_block((uint64_t)i, seed);
+        const double u_phi = unit53(w.x, w.y);
+        const double u_r = unit53(w.z, w.w);
+        const double phi = __dmul_rn(u_phi, kTwoPi);
+        const double r = __ddiv_rn(acosh(__dadd_rn(1.0, __dmul_rn(u_r, p.big))), p.alpha);
+        phi_out[i] = phi;
+        r_out[i] = r;
+        atomicAdd(&sh[band_of(p, r)], 1);
+    }
+    band_hist_flush(p, sh, band_cnt);
+}
+
+__global__ void k_count_bands(Plan p, const double *__restrict__ r, int64_t *__restrict__ band_cnt)
+{
+    __shared__ int sh[HRG_MAX_BANDS];
+    for (int k = threadIdx.x; k < HRG_MAX_BANDS; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride)
+        atomicAdd(&sh[band_of(p, r[i])], 1);
+    band_hist_flush(p, sh, band_cnt);
+}
+
+__global__ void k_bucket_hist(Plan p, const double *__restrict__ r, const double *__restrict__ phi,
+                              int32_t *__restrict__ gbuf, int32_t *__restrict__ cnt)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+        const int band = band_of(p, r[i]);
+        const int64_t g = bucket_of(p, band, angle_key(phi[i]));
+        gbuf[i] = (int32_t)g;
+        atomicAdd(&cnt[g], 1);
+    }
+}
+
+__global__ void k_bucket_scatter(int64_t n, const int32_t *__restrict__ gbuf, const int32_t *__restrict__ start,
+                                 int32_t *__restrict__ cnt, int32_t *__restrict__ perm)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int32_t g = gbuf[i];
+        const int32_t slot = atomicSub(&cnt[g], 1) - 1;
+        perm[start[g] + slot] = (int32_t)i;
+    }
+}
+
+__global__ void k_build_soa(Plan p, const int32_t *__restrict__ perm, const double *__restrict__ r,
+                            const double *__restrict__ phi, uint64_t *__restrict__ A, PMS *__restrict__ pms,
+                            PMS64 *__restrict__ pms64)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.n; k += stride) {
+        const int32_t id = perm[k];
+        const double rr = r[id], ph = phi[id];
+        A[k] = angle_key(ph);
+        pms[k] = scaled_exps(p, rr, id);
+        if (pms64) pms64[k] = scaled_exps64(p, rr, ph);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan: tiles of kTile elements; tile sums scanned recursively.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int64_t kTile = (int64_t)kScanThreads * kScanItems;
+
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T *warp_tot, T *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        T t = lane < nw ? warp_tot[lane] : T(0);
+        T ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < nw) warp_tot[lane] = ti - t;
+        if (lane == nw - 1) *total = ti;
+    }
+    __syncthreads();
+    const T res = inc - v + warp_tot[wid];
+    __syncthreads();
+    return res;
+}
+
+template <typename Tin, typename Tacc>
+__global__ void k_scan_reduce(const Tin *__restrict__ in, int64_t N, Tacc *__restrict__ sums)
+{
+    __shared__ Tacc wt[32];
+    __shared__ Tacc tot;
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    Tacc s = 0;
+    for (int j = 0; j < kScanItems; ++j) {
+        const int64_t i = base + (int64_t)j * kScanThreads + threadIdx.x;
+        if (i < N) s += (Tacc)in[i];
+    }
+    block_exclusive_scan<Tacc>(s, wt, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <typename Tin, typename Tout, typename Tacc>
+__global__ void k_scan_down(const Tin *__restrict__ in, int64_t N, const Tacc *__restrict__ offs,
+                            Tout *__restrict__ out, bool write_total)
+{
+    __shared__ Tacc wt[32];
+    __shared__ Tacc tot;
+    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
+    Tacc v[kScanItems];
+    Tacc s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int64_t i = base + j;
+        v[j] = i < N ? (Tacc)in[i] : Tacc(0);
+        s += v[j];
+    }
+    Tacc run = block_exclusive_scan<Tacc>(s, wt, &tot) + (offs ? offs[blockIdx.x] : Tacc(0));
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int64_t i = base + j;
+        if (i < N) out[i] = (Tout)run;
+        run += v[j];
+    }
+    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[N] = (Tout)run;
+}
+
+template <typename Tin, typename Tout>
+cudaError_t scan_impl(const Tin *in, Tout *out, int64_t N, int64_t *ws, cudaStream_t s)
+{
+    const int64_t tiles = (N + kTile - 1) / kTile;
+    if (N <= 0) {
+        return cudaMemsetAsync(out, 0, sizeof(Tout), s);
+    }
+    if (tiles == 1) {
+        k_scan_down<Tin, Tout, int64_t><<<1, kScanThreads, 0, s>>>(in, N, nullptr, out, true);
+        return cudaGetLastError();
+    }
+    int64_t *sums = ws;
+    int64_t *sums_scan = ws + tiles;
+    k_scan_reduce<Tin, int64_t><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, N, sums);
+    cudaError_t e = scan_impl<int64_t, int64_t>(sums, sums_scan, tiles, ws + 2 * tiles + 1, s);
+    if (e != cudaSuccess) return e;
+    k_scan_down<Tin, Tout, int64_t><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, N, sums_scan, out, true);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t scan_workspace_bytes(int64_t N)
+{
+    size_t words = 0;
+    int64_t m = N;
+    while (m > kTile) {
+        const int64_t t = (m + kTile - 1) / kTile;
+        words += 2 * t + 1;
+        m = t;
+    }
+    return (words + 8) * sizeof(int64_t);
+}
+
+cudaError_t scan_i32_to_i32(const int32_t *in, int32_t *out, int64_t N, void *ws, cudaStream_t s)
+{
+    return scan_impl<int32_t, int32_t>(in, out, N, (int64_t *)ws, s);
+}
+
+cudaError_t scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t N, void *ws, cudaStream_t s)
+{
+    return scan_impl<int32_t, int64_t>(in, out, N, (int64_t *)ws, s);
+}
+
+cudaError_t launch_sample(const Plan &p, uint64_t seed, double *r, double *phi, int64_t *band_cnt, cudaStream_t s)
+{
+    k_sample<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, seed, r, phi, band_cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_bands(const Plan &p, const double *r, const double *, int64_t *band_cnt, cudaStream_t s)
+{
+    k_count_bands<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, r, band_cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi, int32_t *gbuf, int32_t *cnt,
+                               cudaStream_t s)
+{
+    k_bucket_hist<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, r, phi, gbuf, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_scatter(const Plan &p, const int32_t *gbuf, const int32_t *start, int32_t *cnt,
+                                  int32_t *perm, cudaStream_t s)
+{
+    k_bucket_scatter<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p.n, gbuf, start, cnt, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_soa(const Plan &p, const int32_t *perm, const double *r, const double *phi, uint64_t *A,
+                             PMS *pms, PMS64 *pms64, cudaStream_t s)
+{
+    k_build_soa<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, perm, r, phi, A, pms, pms64);
+    return cudaGetLastError();
+}
+
+}  // namespace hrg
