@@ -1,0 +1,335 @@
+"""Benchmark: CSR edges/s of the threshold random hyperbolic graph generator.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+One step is the whole generator on one graph -- radius solve, sampling, band
+structure, degree count, row offsets, neighbour write, row sort -- for the
+workload n = 1e8, alpha = 0.55 (gamma = 2.1), kbar = 16, seed 3 with the FP32
+filter + FP64 recheck, outputs resident in device memory.  ``value`` is
+directed CSR entries (2m) per second over the timed steps.  The plain FP64
+path on the same graph, the end-to-end rate through the host-buffer entry
+point, the roofline of the dominant kernel, the clocks seen during the timed
+region and the CPU oracle's rate on the host cores are reported beside it.
+
+N > 1 (torchrun, one rank per GPU): every rank generates its own graph
+(seed 3 + rank) -- independent problems, no data-path collective, weak
+scaling.  --impl reference times the CPU oracle (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1501_03545_gb300 import workloads as W  # noqa: E402
+
+METRIC = "CSR edges/sec at n=1e8 (FP32-filter vs plain FP64, same GB300), batched graphs/sec, p50/p99"
+UNIT = "edges/s"
+WORKLOAD = W.LARGE
+# CPU-oracle sample: the same alpha, kbar and seed at a size the host cores
+# finish in ~10-30 s (the band algorithm's per-entry cost grows only
+# logarithmically with n).
+ORACLE_SAMPLE_N = 2_000_000
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture, valid
+# only while the kernel source hashes to the recorded value.
+NCU_TRAFFIC = {}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("hrg_query.cu", "hrg_common.cuh", "hrg_points.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1501_03545_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 10:
+                    continue
+                rows.append(f)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        load = [r for r in rows if (num(r[4]) or 0) >= 50] or rows
+        sm = [num(r[1]) for r in load if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in load for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(load)}
+
+
+def oracle_rate(n=ORACLE_SAMPLE_N):
+    """The CPU oracle as it stands (sample + band structure + count + fill),
+    timed on this host's cores: directed entries per second."""
+    import oracle as O
+
+    w = WORKLOAD
+    t0 = time.perf_counter()
+    R = O.solve_radius(n, w.alpha, w.kbar)
+    r, phi = O.sample(n, w.alpha, R, w.seed)
+    b = O.Bands(r, phi, R)
+    off, col = b.csr()
+    b.close()
+    dt = time.perf_counter() - t0
+    return {"value": float(off[-1]) / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "oracle band algorithm, whole pipeline (sample, bands, count, fill) on the same alpha=%g, "
+                      "kbar=%g, seed=%d at n=%d: %d entries in %.2f s" % (w.alpha, w.kbar, w.seed, n,
+                                                                          int(off[-1]), dt),
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    steps = []
+    for _ in range(args.warmup):
+        oracle_rate(args.oracle_n)
+    for _ in range(args.steps):
+        steps.append(oracle_rate(args.oracle_n))
+    secs = sum(s["seconds"] for s in steps)
+    entries = sum(s["value"] * s["seconds"] for s in steps)
+    val = entries / secs
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD.name, "n": args.oracle_n, "alpha": WORKLOAD.alpha,
+                       "kbar": WORKLOAD.kbar, "seed": WORKLOAD.seed, "path": "cpu oracle band algorithm"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": steps[-1]["cores"], "kind": "oracle",
+                             "sample": steps[-1]["sample"]},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--oracle-n", type=int, default=ORACLE_SAMPLE_N)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--n", type=int, default=0, help="profiling only: same alpha/kbar/seed at another n")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1501_03545_gb300 import _lib as H
+
+    H.load()
+    w = WORKLOAD if args.n <= 0 else W.scaled(WORKLOAD, args.n)
+    seed = w.seed + rank
+    ctx = H.Context(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(fp64=False):
+        return H.generate(ctx, w.n, w.alpha, w.kbar, seed, fp64_only=fp64, stream=stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    g = None
+    for _ in range(max(3, args.warmup)):
+        g = step()
+        del g
+    barrier()
+    stats = []
+    entries = 0
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            g = step()
+            entries += g["stats"]["n_entries"]
+            stats.append(g["stats"])
+            del g
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    e = torch.tensor([float(entries)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    value = float(e.item()) / (ms_max / 1e3)
+    last = stats[-1]
+    n_entries = last["n_entries"]
+
+    # stage times (device, CUDA events on the job stream) averaged over the timed steps
+    stage = {k: statistics.mean(s["stage_ms"][k] for s in stats) for k in stats[0]["stage_ms"]}
+
+    # plain FP64 path on the same graph
+    fp64 = None
+    if args.fp64_steps > 0:
+        g = step(fp64=True)
+        del g
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.fp64_steps):
+            g = step(fp64=True)
+            del g
+        b.record(stream)
+        torch.cuda.synchronize()
+        fms = a.elapsed_time(b) / args.fp64_steps
+        fp64 = {"value": n_entries / (fms / 1e3), "unit": UNIT, "ms_per_step": fms}
+
+    # end to end through the host-buffer entry point (D2H of all outputs)
+    e2e = None
+    if args.e2e_steps > 0:
+        n = w.n
+        rh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        ph = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        oh = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
+        ch = torch.empty(int(n_entries * 1.01) + 1024, dtype=torch.int32, pin_memory=True)
+        H.generate_host(ctx, n, w.alpha, w.kbar, seed, rh, ph, oh, ch)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ne, _ = H.generate_host(ctx, n, w.alpha, w.kbar, seed, rh, ph, oh, ch)
+        torch.cuda.synchronize()
+        es = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": ne / es, "unit": UNIT, "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": int(16 * n + 8 * (n + 1) + 4 * ne), "ms_per_step": 1e3 * es}
+        del rh, ph, oh, ch
+
+    # roofline of the dominant kernel group
+    peak, peak_kind = peaks()
+    n = w.n
+    kern = max(("count", "write", "rowsort"), key=lambda k: stage[k])
+    algo = {
+        # count pass: candidate structure read once (A 8 B + FP32 data 16 B), degree written (4 B)
+        "count": 24 * n + 4 * n,
+        # write pass: structure read once, offsets + degree read, the CSR neighbour ids written
+        "write": 24 * n + 12 * n + 4 * n_entries,
+        # row sort: every entry of a row longer than 32 read and written once
+        "rowsort": 8 * n_entries,
+    }[kern]
+    achieved = algo / (stage[kern] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes": algo,
+            "traffic": NCU_TRAFFIC.get((kern, source_hash())),
+            "query_csr_roofline": {
+                "bytes": 4 * n_entries + 8 * (n + 1) + 2 * 16 * n,
+                "ms": stage["count"] + stage["offsets"] + stage["write"] + stage["rowsort"]}}
+    qc = roof["query_csr_roofline"]
+    qc["frac"] = qc["bytes"] / (qc["ms"] / 1e3) / 1e9 / peak
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_rate(args.oracle_n)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64recheck", "data": "synthetic",
+                "config": {"workload": w.name, "n": w.n, "alpha": w.alpha, "kbar": w.kbar, "seed": w.seed,
+                           "path": "fp32 filter + fp64 recheck", "entries_per_step": n_entries,
+                           "undirected_edges_per_s": value / 2,
+                           "l2": "no flush: every step writes and reads >8 GB, far above the 126 MB L2"},
+                "fp64_plain": fp64, "stage_ms": stage, "e2e": e2e, "roofline": roof, "clocks": clocks,
+                "cpu_baseline": cpu, "gpu_launches": last.get("launches", 0) * args.steps,
+                "job": {k: last[k] for k in ("R", "candidates", "rechecks", "bands", "hub_bands", "buckets",
+                                             "hub_queries", "mid_rows", "big_rows", "mu")}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -77,6 +77,7 @@ typedef struct hrg_stats {
      * read-back, bucket counting sort, structure-of-arrays), [2] degree count,
      * [3] row offsets, [4] neighbour write, [5] row sort */
     float stage_ms[6];
+    int32_t launches;            /* kernels this library launched for the job       */
 } hrg_stats;
 
 typedef struct hrg_ctx hrg_ctx;

@@ -490,6 +490,14 @@ extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
     out->big_rows = job->n_big;
     out->mu = job->plan.mu;
     for (int k = 0; k < 6; ++k) out->stage_ms[k] = job->stage_ms[k];
+    // kernels launched: points (1), bucket histogram (1), bucket scan,
+    // scatter (1), structure-of-arrays (1), count (1-2), row-offset scan,
+    // write (1-2), row sorts (mid 1, big 5)
+    const int64_t n = job->plan.n;
+    const int q = (job->p_hub > 0 ? 1 : 0) + (n - job->p_hub > 0 ? 1 : 0);
+    int L = 1 + 1 + scan_launches(job->plan.G) + 1 + 1 + q + scan_launches(n);
+    if (job->finished) L += q + (job->n_mid > 0 ? 1 : 0) + (job->n_big > 0 ? 5 : 0);
+    out->launches = L;
     return HRG_OK;
 }
 

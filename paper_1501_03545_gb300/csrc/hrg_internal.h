@@ -25,6 +25,7 @@ cudaError_t launch_build_soa(const Plan &p, const int32_t *perm, const double *r
 
 // Exclusive prefix sums with the total stored at out[N].
 size_t scan_workspace_bytes(int64_t N);
+int scan_launches(int64_t N);  // kernels one scan of length N launches
 cudaError_t scan_i32_to_i32(const int32_t *in, int32_t *out, int64_t N, void *ws, cudaStream_t s);
 cudaError_t scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t N, void *ws, cudaStream_t s);
 

@@ -201,6 +201,17 @@ cudaError_t scan_impl(const Tin *in, Tout *out, int64_t N, int64_t *ws, cudaStre
 
 }  // namespace
 
+int scan_launches(int64_t N)
+{
+    int k = 1;
+    int64_t m = N;
+    while (m > kTile) {
+        m = (m + kTile - 1) / kTile;
+        k += 2;
+    }
+    return k;
+}
+
 size_t scan_workspace_bytes(int64_t N)
 {
     size_t words = 0;
