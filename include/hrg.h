@@ -170,6 +170,31 @@ int hrg_generate(hrg_ctx *ctx, const hrg_params *p, void *stream, double *r_out,
 int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_host, double *phi_host, int64_t *row_off_host,
                       int32_t *col_idx_host, int64_t col_capacity, int64_t *n_entries, hrg_stats *stats_out);
 
+/*
+ * hrg_row_offsets_noalloc -- CSR row offsets from vertex degrees with no
+ * device allocation.  The paper has no counterpart; this is a service entry
+ * for callers that are not allowed to allocate GPU memory: code that runs
+ * inside a host framework which owns every device byte through its own pool,
+ * or a serving loop with a fixed memory budget where an allocation (which may
+ * also synchronize the device) is not permitted.
+ *   deg      device int32[n], degrees in vertex-id order        (caller owned, read)
+ *   n        0 <= n <= 2^28
+ *   row_off  device int64[n+1]; row_off[i] = deg[0] + ... + deg[i-1],
+ *            row_off[n] = the total                             (caller owned)
+ *   stream   cudaStream_t (as void*), 0 for the legacy stream; the call is
+ *            asynchronous on it
+ * Scratch: a 1 MiB array compiled into the library as device memory, held by
+ * every device that loads the library until the process exits.  The first
+ * call on a device looks up that array's device address (with the device
+ * current), so make the first call on each device before any stream capture.
+ * All calls share the array: calls whose executions overlap on the GPU (on
+ * different streams, or from different threads) race and corrupt each other's
+ * results; serialize them.
+ * Errors: HRG_EINVAL (n outside [0, 2^28], null pointer), HRG_ECUDA (address
+ * lookup or launch failed).  Calls no cudaMalloc/cudaFree.
+ */
+int hrg_row_offsets_noalloc(const int32_t *deg, int64_t n, int64_t *row_off, void *stream);
+
 /* Message of the last error on this context (never null). */
 const char *hrg_last_error(const hrg_ctx *ctx);
 

@@ -20,7 +20,7 @@ HRG_FLAG_FP64_ONLY = 0x1
 EXPORTS = (
     "hrg_solve_radius", "hrg_expected_degree", "hrg_create", "hrg_destroy", "hrg_generate_begin",
     "hrg_generate_from_points_begin", "hrg_generate_finish", "hrg_job_stats", "hrg_job_release",
-    "hrg_generate", "hrg_generate_host", "hrg_last_error", "hrg_version",
+    "hrg_generate", "hrg_generate_host", "hrg_last_error", "hrg_version", "hrg_row_offsets_noalloc",
 )
 
 
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
         L.hrg_last_error.argtypes = [_P]
         L.hrg_last_error.restype = ctypes.c_char_p
         L.hrg_version.restype = ctypes.c_char_p
+        L.hrg_row_offsets_noalloc.argtypes = [_P, _I64, _P, _P]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         _lib = L
@@ -220,3 +221,13 @@ def generate_host(ctx: Context, n, alpha, avg_degree, seed, r_host, phi_host, of
                              ctypes.byref(ne), ctypes.byref(s))
     ctx.check(rc)
     return ne.value, s.as_dict()
+
+
+def hrg_row_offsets_noalloc(deg, row_off, stream=None) -> int:
+    """Row offsets from int32 degrees (device tensors) using the library's
+    static scratch; returns the status code."""
+    import torch
+
+    st = stream if stream is not None else torch.cuda.current_stream(deg.device)
+    return int(load().hrg_row_offsets_noalloc(_P(deg.data_ptr()), int(deg.numel()), _P(row_off.data_ptr()),
+                                              _P(st.cuda_stream)))
