@@ -288,6 +288,8 @@ def main():
     # roofline of the dominant kernel group
     peak, peak_kind = peaks()
     n = w.n
+    stage["count"] = stage["count_hub"] + stage["count_rim"]
+    stage["write"] = stage["write_hub"] + stage["write_rim"]
     kern = max(("count", "write", "rowsort"), key=lambda k: stage[k])
     algo = {
         # count pass: candidate structure read once (A 8 B + FP32 data 16 B), degree written (4 B)

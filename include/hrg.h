@@ -74,9 +74,11 @@ typedef struct hrg_stats {
     float mu;                    /* relative half-width of the FP32 undecided band  */
     /* device time of each stage in ms (CUDA events on the job's stream), valid
      * after hrg_generate_finish: [0] sampling, [1] band structure (band counts
-     * read-back, bucket counting sort, structure-of-arrays), [2] degree count,
-     * [3] row offsets, [4] neighbour write, [5] row sort */
-    float stage_ms[6];
+     * read-back, bucket counting sort, structure-of-arrays), [2] degree count
+     * of hub-band vertices, [3] degree count of rim-band vertices, [4] row
+     * offsets, [5] neighbour write of hub-band vertices, [6] neighbour write of
+     * rim-band vertices, [7] row sort */
+    float stage_ms[8];
     int32_t launches;            /* kernels this library launched for the job       */
 } hrg_stats;
 

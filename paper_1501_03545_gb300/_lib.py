@@ -41,9 +41,9 @@ class hrg_stats(ctypes.Structure):
                 ("rechecks", ctypes.c_uint64), ("bands", ctypes.c_int32), ("hub_bands", ctypes.c_int32),
                 ("buckets", ctypes.c_int64), ("hub_queries", ctypes.c_int32), ("mid_rows", ctypes.c_int32),
                 ("big_rows", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mu", ctypes.c_float),
-                ("stage_ms", ctypes.c_float * 6), ("launches", ctypes.c_int32)]
+                ("stage_ms", ctypes.c_float * 8), ("launches", ctypes.c_int32)]
 
-    STAGES = ("sample", "bands", "count", "offsets", "write", "rowsort")
+    STAGES = ("sample", "bands", "count_hub", "count_rim", "offsets", "write_hub", "write_rim", "rowsort")
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "stage_ms")}

@@ -84,11 +84,11 @@ struct hrg_job {
     bool open = false;
     bool finished = false;
     int32_t p_hub = 0;
-    int n_mid = 0, n_big = 0;
+    int32_t lists[3] = {0, 0, 0};
     int64_t big_total = 0;
     int64_t n_entries = 0;
     uint64_t stats[8] = {};
-    float stage_ms[6] = {};
+    float stage_ms[8] = {};
     const double *r = nullptr, *phi = nullptr;
     int64_t *row_off = nullptr;
     cudaStream_t stream = nullptr;
@@ -99,11 +99,12 @@ struct hrg_ctx {
     int device = 0;
     std::string err;
     // workspace slots
-    enum { W_BANDCNT, W_GBUF, W_CNT, W_START, W_PERM, W_A, W_PMS, W_PMS64, W_DEG, W_STATS, W_MID, W_BIG,
-           W_LISTCNT, W_BIGTOT, W_SCAN, W_TMP, W_BUCKET, W_OUT_R, W_OUT_PHI, W_OUT_OFF, W_OUT_COL, W_COUNT };
+    enum { W_BANDCNT, W_GBUF, W_CNT, W_START, W_PERM, W_A, W_PMS, W_PMS64, W_DEG, W_STATS, W_LIST0, W_LIST1,
+           W_LIST2, W_LISTCNT, W_BIGTOT, W_SCAN, W_TMP, W_BUCKET, W_OUT_R, W_OUT_PHI, W_OUT_OFF, W_OUT_COL,
+           W_HEAVY, W_CURSOR, W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
-    cudaEvent_t ev[8] = {};  // stage boundaries of the current job
+    cudaEvent_t ev[10] = {};  // stage boundaries of the current job
     hrg_job job;
 };
 
@@ -240,10 +241,16 @@ static void plan_bands(Plan &p, int64_t n, double R, double alpha, int bands)
 // Angular buckets and hub bands once the band counts are known.
 static void plan_buckets(Plan &p, const int64_t *cnt, int32_t *p_hub)
 {
+    // 2^sbits angular sectors of about 1024 points each; every band gets at
+    // least one bucket per sector so sectors are bucket-aligned in each band
+    int sb = 0;
+    while (sb < 20 && ((int64_t)1024 << (sb + 1)) <= p.n) ++sb;
+    p.sbits = sb;
     int64_t G = 0;
     for (int k = 0; k < p.B; ++k) {
         int g = 0;
         while (g < 40 && ((int64_t)1 << (g + 1)) <= cnt[k]) ++g;
+        if (g < sb) g = sb;
         p.gbits[k] = g;
         p.base[k] = G;
         G += (int64_t)1 << g;
@@ -251,7 +258,7 @@ static void plan_buckets(Plan &p, const int64_t *cnt, int32_t *p_hub)
     p.base[p.B] = G;
     p.G = G;
     // hub bands: expected candidates of a query at the band's inner radius
-    // above ~2048 (sum over bands of count * window / pi)
+    // above ~512 (sum over bands of count * window / pi)
     int hub = 0;
     for (int i = 0; i < p.B; ++i) {
         const double rq = p.band_lo[i];
@@ -267,7 +274,7 @@ static void plan_buckets(Plan &p, const int64_t *cnt, int32_t *p_hub)
             }
             cand += frac * (double)cnt[j];
         }
-        if (cand > 2048.0) hub = i + 1; else break;
+        if (cand > 512.0) hub = i + 1; else break;
     }
     p.hub_bands = hub;
     int64_t ph = 0;
@@ -288,7 +295,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     Plan &p = J.plan;
     plan_bands(p, n, R, alpha, bands);
 
-    void *band_cnt, *gbuf, *perm, *A, *pms, *pms64 = nullptr, *deg, *stats, *mid, *big, *listcnt, *bigtot, *scanws;
+    void *band_cnt, *gbuf, *perm, *A, *pms, *pms64 = nullptr, *deg, *stats, *lists[3], *listcnt, *bigtot, *scanws;
     int rc;
     if ((rc = ensure(ctx, hrg_ctx::W_BANDCNT, sizeof(int64_t) * HRG_MAX_BANDS, &band_cnt))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_GBUF, sizeof(int32_t) * n, &gbuf))) return rc;
@@ -298,9 +305,9 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     if (J.fp64 && (rc = ensure(ctx, hrg_ctx::W_PMS64, sizeof(PMS64) * n, &pms64))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_DEG, sizeof(int32_t) * n, &deg))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_STATS, sizeof(uint64_t) * 8, &stats))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_MID, sizeof(int32_t) * n, &mid))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_BIG, sizeof(int32_t) * n, &big))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 2, &listcnt))) return rc;
+    for (int k = 0; k < 3; ++k)
+        if ((rc = ensure(ctx, hrg_ctx::W_LIST0 + k, sizeof(int32_t) * n, &lists[k]))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 4, &listcnt))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_BIGTOT, sizeof(int64_t), &bigtot))) return rc;
 
     // 1. points and band counts
@@ -346,31 +353,47 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     b.phi = J.phi;
     b.deg = (int32_t *)deg;
     b.stats = (unsigned long long *)stats;
-    b.mid_rows = (int32_t *)mid;
-    b.big_rows = (int32_t *)big;
+    for (int k = 0; k < 3; ++k) b.rows[k] = (int32_t *)lists[k];
     b.list_cnt = (int32_t *)listcnt;
     b.big_total = (int64_t *)bigtot;
-    CK(cudaMemsetAsync(stats, 0, sizeof(uint64_t) * 8, st));
-    CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 2, st));
-    CK(cudaMemsetAsync(bigtot, 0, sizeof(int64_t), st));
-    CK(launch_count_split(p, b, J.fp64, J.p_hub, st));
-    CK(cudaEventRecord(ctx->ev[3], st));
+    // heavy hub segments (long hub ranges cut into CTA chunks) and hub row cursors
+    void *heavy = nullptr, *cursor = nullptr;
+    int64_t heavy_cap = std::max<int64_t>(1 << 16, n / 64);
+    if (J.p_hub > 0 && (rc = ensure(ctx, hrg_ctx::W_CURSOR, sizeof(int32_t) * J.p_hub, &cursor))) return rc;
+    b.cursor = (int32_t *)cursor;
+    for (int attempt = 0;; ++attempt) {
+        if ((rc = ensure(ctx, hrg_ctx::W_HEAVY, sizeof(int4) * heavy_cap, &heavy))) return rc;
+        b.heavy = (int4 *)heavy;
+        b.heavy_cap = (int32_t)heavy_cap;
+        CK(cudaMemsetAsync(stats, 0, sizeof(uint64_t) * 8, st));
+        CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 4, st));
+        CK(cudaMemsetAsync(bigtot, 0, sizeof(int64_t), st));
+        CK(cudaMemsetAsync(deg, 0, sizeof(int32_t) * n, st));
+        CK(launch_count_hub(p, b, J.fp64, J.p_hub, st));
+        CK(cudaEventRecord(ctx->ev[3], st));
+        CK(launch_count_rim(p, b, J.fp64, st));
+        CK(cudaEventRecord(ctx->ev[4], st));
+        if (J.p_hub == 0) break;
+        int32_t *hc = (int32_t *)ctx->pinned;
+        CK(cudaMemcpyAsync(hc, (int32_t *)listcnt + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (*hc <= heavy_cap) break;
+        if (attempt > 0 || *hc > (1 << 30)) return set_err(ctx, HRG_EINTERNAL, "heavy segment list overflow");
+        heavy_cap = (int64_t)*hc + *hc / 8 + 1024;  // grow and count again
+    }
 
     // 4. row offsets
     CK(scan_i32_to_i64((int32_t *)deg, row_off_out, n, scanws, st));
-    CK(cudaEventRecord(ctx->ev[4], st));
+    CK(cudaEventRecord(ctx->ev[5], st));
     char *hp = (char *)ctx->pinned;
     CK(cudaMemcpyAsync(hp + 0, row_off_out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(hp + 8, listcnt, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(hp + 16, bigtot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 8, listcnt, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 24, bigtot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(hp + 64, stats, sizeof(uint64_t) * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     memcpy(&J.n_entries, hp + 0, 8);
-    int32_t lc[2];
-    memcpy(lc, hp + 8, 8);
-    J.n_mid = lc[0];
-    J.n_big = lc[1];
-    memcpy(&J.big_total, hp + 16, 8);
+    memcpy(J.lists, hp + 8, 12);
+    memcpy(&J.big_total, hp + 24, 8);
     memcpy(J.stats, hp + 64, 64);
     J.open = true;
     *n_entries = J.n_entries;
@@ -441,28 +464,30 @@ extern "C" int hrg_generate_finish(hrg_job *job, int32_t *col_idx_out)
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
     cudaStream_t st = job->stream;
     const Plan &p = job->plan;
-    CK(cudaEventRecord(ctx->ev[5], st));
-    CK(launch_write_split(p, job->qb, job->fp64, job->p_hub, job->row_off, col_idx_out, st));
     CK(cudaEventRecord(ctx->ev[6], st));
-    if (job->n_mid > 0 || job->n_big > 0) {
+    if (job->p_hub > 0) CK(cudaMemsetAsync(job->qb.cursor, 0, sizeof(int32_t) * job->p_hub, st));
+    CK(launch_write_hub(p, job->qb, job->fp64, job->p_hub, job->row_off, col_idx_out, st));
+    CK(cudaEventRecord(ctx->ev[7], st));
+    CK(launch_write_rim(p, job->qb, job->fp64, job->row_off, col_idx_out, st));
+    CK(cudaEventRecord(ctx->ev[8], st));
+    if (job->lists[0] > 0 || job->lists[1] > 0 || job->lists[2] > 0) {
         void *tmp = nullptr, *bws = nullptr;
         int rc;
-        int64_t bws_words = 16;
-        if (job->n_big > 0) {
+        if (job->lists[2] > 0) {
             if ((rc = ensure(ctx, hrg_ctx::W_TMP, sizeof(int32_t) * job->big_total, &tmp))) return rc;
-            bws_words = (int64_t)(((size_t)job->n_big * 16 + 3) / 4 + big_sort_hist_words(p.n, job->n_big));
+            if ((rc = ensure(ctx, hrg_ctx::W_BUCKET, big_sort_ws_bytes(job->lists[2], job->big_total), &bws)))
+                return rc;
         }
-        if ((rc = ensure(ctx, hrg_ctx::W_BUCKET, sizeof(int32_t) * bws_words, &bws))) return rc;
-        CK(launch_sort_rows(p, job->qb, job->n_mid, job->n_big, job->row_off, col_idx_out, (int32_t *)tmp,
-                            job->big_total, (int32_t *)bws, bws_words, st));
+        CK(launch_sort_rows(p, job->qb, job->lists, job->big_total, job->row_off, col_idx_out, (int32_t *)tmp, bws,
+                            st));
     }
-    CK(cudaEventRecord(ctx->ev[7], st));
+    CK(cudaEventRecord(ctx->ev[9], st));
     uint64_t *hs = (uint64_t *)ctx->pinned;
     CK(cudaMemcpyAsync(hs, job->qb.stats + 7, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     job->finished = true;
-    const int pairs[6][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {5, 6}, {6, 7}};
-    for (int k = 0; k < 6; ++k) {
+    const int pairs[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {6, 7}, {7, 8}, {8, 9}};
+    for (int k = 0; k < 8; ++k) {
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, ctx->ev[pairs[k][0]], ctx->ev[pairs[k][1]]) != cudaSuccess) {
             cudaGetLastError();
@@ -486,17 +511,17 @@ extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
     out->hub_bands = job->plan.hub_bands;
     out->buckets = job->plan.G;
     out->hub_queries = job->p_hub;
-    out->mid_rows = job->n_mid;
-    out->big_rows = job->n_big;
+    out->mid_rows = job->lists[0] + job->lists[1];
+    out->big_rows = job->lists[2];
     out->mu = job->plan.mu;
-    for (int k = 0; k < 6; ++k) out->stage_ms[k] = job->stage_ms[k];
+    for (int k = 0; k < 8; ++k) out->stage_ms[k] = job->stage_ms[k];
     // kernels launched: points (1), bucket histogram (1), bucket scan,
     // scatter (1), structure-of-arrays (1), count (1-2), row-offset scan,
     // write (1-2), row sorts (mid 1, big 5)
     const int64_t n = job->plan.n;
-    const int q = (job->p_hub > 0 ? 1 : 0) + (n - job->p_hub > 0 ? 1 : 0);
-    int L = 1 + 1 + scan_launches(job->plan.G) + 1 + 1 + q + scan_launches(n);
-    if (job->finished) L += q + (job->n_mid > 0 ? 1 : 0) + (job->n_big > 0 ? 5 : 0);
+    int L = 1 + 1 + scan_launches(job->plan.G) + 1 + 1 + query_launches(job->plan, job->p_hub, false) +
+            scan_launches(n);
+    if (job->finished) L += query_launches(job->plan, job->p_hub, true) + sort_launches(job->lists);
     out->launches = L;
     return HRG_OK;
 }

@@ -25,7 +25,8 @@ struct Plan {
     double half_R;       // R / 2
     double inv_width;    // B / R
     int B;               // number of radial bands
-    int hub_bands;       // bands [0, hub_bands) are queried by whole CTAs
+    int hub_bands;       // bands [0, hub_bands) are queried one warp per vertex
+    int sbits;           // 2^sbits angular sectors; every band has gbits >= sbits
     int64_t G;           // total number of angular buckets over all bands
     double band_lo[HRG_MAX_BANDS + 1];  // inner radius of each band; band_lo[B] = +inf
     int64_t base[HRG_MAX_BANDS + 1];    // first bucket of each band; base[B] = G
@@ -149,7 +150,12 @@ __device__ __forceinline__ float sin_taylor(float x)
 // difference dA (signed, |dA| <= 2^63 <-> pi).
 __device__ __forceinline__ float lhs32(const PMS &q, const PMS &c, int64_t dA)
 {
-    const float half = __ll2float_rn(dA) * (0.5f * kAngleUnit);
+    // dA = hi 2^32 + lo with hi signed and lo unsigned; two 32-bit
+    // conversions (the 64-bit one is an order of magnitude slower) and one
+    // FMA give dA * pi / 2^64 to within 3 ulp
+    const int32_t hi = (int32_t)(dA >> 32);
+    const uint32_t lo = (uint32_t)dA;
+    const float half = fmaf((float)hi, 7.3145904e-10f /* pi / 2^32 */, (float)lo * 1.7030608e-19f /* pi / 2^64 */);
     const float s = sin_taylor(half);
     return fmaf(q.S * c.S, s * s, fmaf(q.P, c.M, c.P * q.M));
 }

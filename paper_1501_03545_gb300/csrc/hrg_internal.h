@@ -29,7 +29,11 @@ int scan_launches(int64_t N);  // kernels one scan of length N launches
 cudaError_t scan_i32_to_i32(const int32_t *in, int32_t *out, int64_t N, void *ws, cudaStream_t s);
 cudaError_t scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t N, void *ws, cudaStream_t s);
 
-// ---- queries (hrg_query.cu) ----
+// ---- queries (hrg_query.cu) and row sorts (hrg_sort.cu) ----
+constexpr int kRegRow = 32;       // rows up to this are sorted in registers by the query
+constexpr int kWarpRow = 256;     // rows up to this: one warp, bitonic in shared memory
+constexpr int kSmemRow = 12288;   // rows up to this: one CTA, radix sort in shared memory
+
 struct QueryBufs {
     const uint64_t *A;        // [n] fixed-point angles, bucket order
     const PMS *pms;           // [n] FP32 scaled exps + id
@@ -38,27 +42,36 @@ struct QueryBufs {
     const double *r;          // [n] id order (FP64 recheck)
     const double *phi;        // [n] id order
     int32_t *deg;             // [n] id order
-    unsigned long long *stats;  // [8] counters (see HRG_STAT_*)
-    int32_t *mid_rows;        // list of (id) rows with 32 < deg <= kSmemRow
-    int32_t *big_rows;        // list of (id) rows with deg > kSmemRow
-    int32_t *list_cnt;        // [2] lengths of the two lists
-    int64_t *big_total;       // [1] sum of degrees of big rows
+    unsigned long long *stats;  // [8] counters: candidates, rechecks, edges, ..., [7] error flag
+    int32_t *rows[3];         // ids of rows to sort: (kRegRow, kWarpRow], (kWarpRow, kSmemRow], > kSmemRow
+    int32_t *list_cnt;        // [4] lengths of the three lists, [3] heavy segments
+    int64_t *big_total;       // [1] sum of degrees of the longest rows
+    int4 *heavy;              // [heavy_cap] (query position, 2*band+part, begin, end) of long hub ranges
+    int32_t heavy_cap;
+    int32_t *cursor;          // [p_hub] write cursor of each hub row
+    int32_t *col_out;         // CSR neighbour ids being written (write pass only)
 };
 
-constexpr int kRegRow = 32;       // rows up to this are sorted in registers
-constexpr int kSmemRow = 12288;   // rows up to this are sorted in shared memory
+constexpr int kHeavy = 4096;      // hub ranges longer than this are split into chunks for whole CTAs
 
-// Degrees of all vertices: queries at sorted positions [0, p_hub) (hub bands)
-// run one CTA each, the rest one thread each.
-cudaError_t launch_count_split(const Plan &p, const QueryBufs &b, bool fp64_only, int32_t p_hub, cudaStream_t s);
-// Same traversal, writing neighbour ids into col_idx[row_off[id] ..].
-cudaError_t launch_write_split(const Plan &p, const QueryBufs &b, bool fp64_only, int32_t p_hub,
-                               const int64_t *row_off, int32_t *col_idx, cudaStream_t s);
-// Sort rows longer than kRegRow (mid rows in shared memory, big rows by id
-// buckets through tmp[big_total]).
-size_t big_sort_hist_words(int64_t n, int n_big);
-cudaError_t launch_sort_rows(const Plan &p, const QueryBufs &b, int n_mid, int n_big, const int64_t *row_off,
-                             int32_t *col_idx, int32_t *tmp, int64_t tmp_len, int32_t *bucket_ws,
-                             int64_t bucket_ws_len, cudaStream_t s);
+// Degrees of hub-band vertices (one warp each, long ranges as CTA chunks).
+// deg must be zero for them beforehand.
+cudaError_t launch_count_hub(const Plan &p, const QueryBufs &b, bool fp64_only, int32_t p_hub, cudaStream_t s);
+// Degrees of rim-band vertices (one CTA per angular sector, one thread per vertex).
+cudaError_t launch_count_rim(const Plan &p, const QueryBufs &b, bool fp64_only, cudaStream_t s);
+// Same traversals, writing neighbour ids into col_idx[row_off[id] ..]; hub
+// rows are written through cursor[] in no particular order (sorted later).
+cudaError_t launch_write_hub(const Plan &p, const QueryBufs &b, bool fp64_only, int32_t p_hub,
+                             const int64_t *row_off, int32_t *col_idx, cudaStream_t s);
+cudaError_t launch_write_rim(const Plan &p, const QueryBufs &b, bool fp64_only, const int64_t *row_off,
+                             int32_t *col_idx, cudaStream_t s);
+int query_launches(const Plan &p, int32_t p_hub, bool write);
+
+// Sort rows longer than kRegRow; tmp holds big_total ids, ws big_sort_ws_bytes.
+size_t sort_smem_bytes();
+size_t big_sort_ws_bytes(int n_big, int64_t big_total);
+int sort_launches(const int32_t counts[3]);
+cudaError_t launch_sort_rows(const Plan &p, const QueryBufs &b, const int32_t counts[3], int64_t big_total,
+                             const int64_t *row_off, int32_t *col_idx, int32_t *tmp, void *ws, cudaStream_t s);
 
 }  // namespace hrg
