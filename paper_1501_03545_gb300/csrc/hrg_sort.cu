@@ -4,11 +4,12 @@
 // canonical CSR lists each row ascending, so rows longer than kRegRow (sorted
 // in registers by the query itself) are sorted here:
 //   * kRegRow < d <= kWarpRow:  one warp per row, bitonic sort in shared memory;
-//   * kWarpRow < d <= kSmemRow: one CTA per row, stable LSD radix sort in
-//     shared memory (8-bit digits, ranks within a warp from __match_any_sync);
+//   * kWarpRow < d <= kSmemRow: one CTA per row, bucket sort in shared memory
+//     (the ids of a row are spread evenly over [0, n), so ~d/2 value buckets
+//     hold ~2 ids each);
 //   * d > kSmemRow: the row's ids are split by value into buckets of expected
 //     size <= 4096 (bucket k holds ids in [k n / nbk, (k+1) n / nbk)), every
-//     bucket is sorted by the CTA radix sort; a bucket that still exceeds
+//     bucket is sorted by the CTA bucket sort; a bucket that still exceeds
 //     kSmemRow (only for id-clustered injected point sets) is sorted by a
 //     bitonic network in global memory.
 #include <cstdio>
@@ -20,11 +21,7 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kWarps = kSortThreads / 32;
-
-__device__ __forceinline__ int bits_for(uint32_t range)
-{
-    return range <= 1 ? 1 : 32 - __clz(range - 1);
-}
+constexpr int kSetupThreads = 1024;  // k_big_setup needs whole warps (shuffle scans)
 
 // --------------------------------------------------------------------------
 // Warp bitonic sort of m (power of two) keys in shared memory.
@@ -65,100 +62,112 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__res
 }
 
 // --------------------------------------------------------------------------
-// Stable CTA LSD radix sort of m <= kSmemRow unsigned keys in shared memory.
-// keys/tmp: shared arrays of kSmemRow; cnt: [kWarps][256] shared counters.
-// Returns the array that holds the sorted keys.
+// CTA bucket sort of m <= kSmemRow keys in [lo, lo + range): the ids of a
+// row are spread evenly over their range, so ~m/2 equal-width buckets hold ~2
+// keys each.  Count (shared atomics), scan, scatter, then every bucket is
+// sorted on its own: by one thread (insertion) up to 32 keys, by one warp
+// (bitonic) beyond, so skewed inputs stay correct.
 // --------------------------------------------------------------------------
-__device__ uint32_t *cta_radix_sort(uint32_t *keys, uint32_t *tmp, uint32_t (*cnt)[256], uint32_t *dsum, int m,
-                                    int bits)
-{
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    int chunk = (m + kWarps - 1) / kWarps;
-    chunk = (chunk + 31) & ~31;
-    const int lo = w * chunk, hi = min(m, lo + chunk);
-    uint32_t *src = keys, *dst = tmp;
-    for (int shift = 0; shift < bits; shift += 8) {
-        for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&cnt[0][0])[i] = 0;
-        __syncthreads();
-        // per-warp digit counts
-        for (int g = lo; g < hi; g += 32) {
-            const int i = g + lane;
-            const bool v = i < hi;
-            const uint32_t d = v ? (src[i] >> shift) & 255u : 256u + lane;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (v && (peers & lt) == 0) cnt[w][d] += __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        // offsets, digit-major then warp: thread t owns digit t
-        {
-            const int t = threadIdx.x;
-            uint32_t tot = 0;
-            for (int ww = 0; ww < kWarps; ++ww) tot += cnt[ww][t];
-            // block exclusive scan of tot over the 256 digits
-            uint32_t inc = tot;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            if (lane == 31) dsum[w] = inc;
-            __syncthreads();
-            if (t < 32) {
-                const uint32_t v = t < kWarps ? dsum[t] : 0u;
-                uint32_t vi = v;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, vi, o);
-                    if (t >= o) vi += y;
-                }
-                if (t < kWarps) dsum[t] = vi - v;
-            }
-            __syncthreads();
-            uint32_t run = inc - tot + dsum[w];
-            for (int ww = 0; ww < kWarps; ++ww) {
-                const uint32_t c = cnt[ww][t];
-                cnt[ww][t] = run;
-                run += c;
-            }
-        }
-        __syncthreads();
-        // stable scatter
-        for (int g = lo; g < hi; g += 32) {
-            const int i = g + lane;
-            const bool v = i < hi;
-            const uint32_t key = v ? src[i] : 0u;
-            const uint32_t d = v ? (key >> shift) & 255u : 256u + lane;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            uint32_t pos = 0;
-            if (v) pos = cnt[w][d] + __popc(peers & lt);
-            __syncwarp();
-            if (v && (peers & lt) == 0) cnt[w][d] += __popc(peers);
-            if (v) dst[pos] = key;
-            __syncwarp();
-        }
-        __syncthreads();
-        uint32_t *t2 = src;
-        src = dst;
-        dst = t2;
-    }
-    return src;
-}
+constexpr int kMaxSortBuckets = 8192;
 
 struct SortSmem {
-    uint32_t keys[kSmemRow];
     uint32_t tmp[kSmemRow];
-    uint32_t cnt[kWarps][256];
-    uint32_t dsum[32];
+    uint32_t cnt[kMaxSortBuckets + 1];
+    uint32_t wsum[kWarps];
 };
 
-__device__ void sort_span(SortSmem &S, const int32_t *src, int32_t *dst, int m, int32_t lo, int bits)
+__device__ __forceinline__ uint32_t key_bucket(uint32_t k, uint32_t nb, uint32_t range)
 {
-    for (int i = threadIdx.x; i < m; i += kSortThreads) S.keys[i] = (uint32_t)(src[i] - lo);
+    return (uint32_t)(((uint64_t)k * nb) / range);
+}
+
+// in-place exclusive scan of c[0..nb) (nb <= kMaxSortBuckets) by the whole CTA
+__device__ void cta_exclusive_scan(uint32_t *c, uint32_t nb, uint32_t *wsum)
+{
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t per = (nb + kSortThreads - 1) / kSortThreads;
+    const uint32_t b0 = min(nb, t * per), b1 = min(nb, b0 + per);
+    uint32_t s = 0;
+    for (uint32_t i = b0; i < b1; ++i) s += c[i];
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
     __syncthreads();
-    const uint32_t *out = cta_radix_sort(S.keys, S.tmp, S.cnt, S.dsum, m, bits);
-    for (int i = threadIdx.x; i < m; i += kSortThreads) dst[i] = (int32_t)out[i] + lo;
+    if (t == 0) {
+        uint32_t acc = 0;
+        for (int k = 0; k < kWarps; ++k) { const uint32_t v = wsum[k]; wsum[k] = acc; acc += v; }
+    }
+    __syncthreads();
+    uint32_t run = inc - s + wsum[w];
+    for (uint32_t i = b0; i < b1; ++i) { const uint32_t v = c[i]; c[i] = run; run += v; }
+    __syncthreads();
+}
+
+// warp bitonic sort of a[0..L) in shared memory, any L (positions >= L act as
+// +infinity: the first step of each merge pairs i with its mirror, so every
+// block sorts ascending and those positions never move)
+__device__ void warp_bitonic_any(uint32_t *a, int L, int lane)
+{
+    int M = 1;
+    while (M < L) M <<= 1;
+    for (int kk = 2; kk <= M; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < M; i += 32) {
+                const int l = (j == (kk >> 1)) ? (i ^ (kk - 1)) : (i ^ j);
+                if (l > i && l < L) {
+                    const uint32_t x = a[i], y = a[l];
+                    if (x > y) { a[i] = y; a[l] = x; }
+                }
+            }
+            __syncwarp();
+        }
+}
+
+__device__ void sort_span(SortSmem &S, const int32_t *src, int32_t *dst, int m, int32_t lo, uint32_t range)
+{
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t nb = 1;
+    while (nb * 4 <= (uint32_t)m && nb < kMaxSortBuckets) nb <<= 1;
+    if (range == 0) range = 1;
+    for (uint32_t i = t; i <= nb; i += kSortThreads) S.cnt[i] = 0;
+    __syncthreads();
+    for (int i = t; i < m; i += kSortThreads) atomicAdd(&S.cnt[key_bucket((uint32_t)(src[i] - lo), nb, range)], 1u);
+    __syncthreads();
+    cta_exclusive_scan(S.cnt, nb, S.wsum);
+    for (int i = t; i < m; i += kSortThreads) {
+        const uint32_t k = (uint32_t)(src[i] - lo);
+        S.tmp[atomicAdd(&S.cnt[key_bucket(k, nb, range)], 1u)] = k;
+    }
+    __syncthreads();
+    // bucket b now spans [cnt[b-1], cnt[b]) (cnt[-1] = 0)
+    for (uint32_t b = t; b < nb; b += kSortThreads) {
+        const uint32_t s0 = b ? S.cnt[b - 1] : 0u, e0 = S.cnt[b];
+        if (e0 - s0 > 1 && e0 - s0 <= 32) {
+            for (uint32_t i = s0 + 1; i < e0; ++i) {
+                const uint32_t v = S.tmp[i];
+                uint32_t k = i;
+                while (k > s0 && S.tmp[k - 1] > v) { S.tmp[k] = S.tmp[k - 1]; --k; }
+                S.tmp[k] = v;
+            }
+        }
+    }
+    for (uint32_t b0 = w * 32; b0 < nb; b0 += kWarps * 32) {
+        const uint32_t b = b0 + lane;
+        const uint32_t s0 = (b < nb && b) ? S.cnt[b - 1] : 0u, e0 = b < nb ? S.cnt[b] : 0u;
+        unsigned big = __ballot_sync(0xffffffffu, b < nb && e0 - s0 > 32);
+        while (big) {
+            const int src_lane = __ffs(big) - 1;
+            big &= big - 1;
+            const uint32_t bs = __shfl_sync(0xffffffffu, s0, src_lane), be = __shfl_sync(0xffffffffu, e0, src_lane);
+            warp_bitonic_any(S.tmp + bs, (int)(be - bs), lane);
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < m; i += kSortThreads) dst[i] = (int32_t)S.tmp[i] + lo;
     __syncthreads();
 }
 
@@ -174,29 +183,57 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_cta_rows(const int32_t *_
     const int32_t id = rows[r];
     const int64_t base = row_off[id];
     const int d = (int)(row_off[id + 1] - base);
-    sort_span(S, col_idx + base, col_idx + base, d, 0, bits_for((uint32_t)n));
+    sort_span(S, col_idx + base, col_idx + base, d, 0, (uint32_t)n);
 }
 
 // --------------------------------------------------------------------------
 // Big rows.
 // --------------------------------------------------------------------------
 struct BigRow { int64_t tmp_off; int64_t hist_off; int32_t nbk; int32_t id; };
-struct Item { int64_t src; int64_t dst; int32_t len; int32_t lo; int32_t bits; int32_t pad; };
+struct Item { int64_t src; int64_t dst; int32_t len; int32_t lo; uint32_t range; int32_t pad; };
 
-__global__ void k_big_setup(const int32_t *__restrict__ rows, int n_big, const int64_t *__restrict__ row_off,
-                            BigRow *__restrict__ br)
+// offsets of the big rows' ids (tmp) and bucket counters (hist): one CTA,
+// chunked prefix sums over the rows
+__global__ void __launch_bounds__(kSetupThreads) k_big_setup(const int32_t *__restrict__ rows, int n_big,
+                                                    const int64_t *__restrict__ row_off, BigRow *__restrict__ br)
 {
-    // serial prefix over the (few) big rows
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    int64_t toff = 0, hoff = 0;
-    for (int k = 0; k < n_big; ++k) {
-        const int32_t id = rows[k];
-        const int64_t d = row_off[id + 1] - row_off[id];
-        int32_t nbk = 2;
-        while ((int64_t)nbk * 4096 < d) nbk <<= 1;
-        br[k] = BigRow{toff, hoff, nbk, id};
-        toff += d;
-        hoff += 2 * (int64_t)nbk;
+    __shared__ long long s_t[32], s_h[32];
+    __shared__ long long carry_t, carry_h;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) { carry_t = 0; carry_h = 0; }
+    __syncthreads();
+    for (int k0 = 0; k0 < n_big; k0 += blockDim.x) {
+        const int k = k0 + t;
+        long long d = 0, h = 0;
+        int32_t id = 0, nbk = 0;
+        if (k < n_big) {
+            id = rows[k];
+            d = row_off[id + 1] - row_off[id];
+            nbk = 2;
+            while ((long long)nbk * 4096 < d) nbk <<= 1;
+            h = 2 * (long long)nbk;
+        }
+        long long it = d, ih = h;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long yt = __shfl_up_sync(0xffffffffu, it, o), yh = __shfl_up_sync(0xffffffffu, ih, o);
+            if (lane >= o) { it += yt; ih += yh; }
+        }
+        if (lane == 31) { s_t[w] = it; s_h[w] = ih; }
+        __syncthreads();
+        if (t == 0) {
+            long long at = carry_t, ah = carry_h;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+                const long long vt = s_t[q], vh = s_h[q];
+                s_t[q] = at; s_h[q] = ah;
+                at += vt; ah += vh;
+            }
+            carry_t = at;
+            carry_h = ah;
+        }
+        __syncthreads();
+        if (k < n_big) br[k] = BigRow{s_t[w] + it - d, s_h[w] + ih - h, nbk, id};
+        __syncthreads();
     }
 }
 
@@ -246,7 +283,7 @@ __global__ void k_big_scan(const BigRow *__restrict__ br, const int64_t *__restr
             if (v > 0) {
                 const int32_t lo = (int32_t)(((int64_t)i * n + R.nbk - 1) / R.nbk);
                 const int32_t hi = (int32_t)(((int64_t)(i + 1) * n + R.nbk - 1) / R.nbk);
-                Item it{R.tmp_off + st, rbase + st, v, lo, bits_for((uint32_t)(hi - lo)), 0};
+                Item it{R.tmp_off + st, rbase + st, v, lo, (uint32_t)(hi - lo), 0};
                 if (v <= kSmemRow) items[atomicAdd(n_items, 1)] = it;
                 else slow[atomicAdd(n_slow, 1)] = it;
             }
@@ -281,7 +318,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_items(const Item *__restr
     const int32_t nit = *n_items;
     for (int32_t k = blockIdx.x; k < nit; k += gridDim.x) {
         const Item it = items[k];
-        sort_span(S, tmp + it.src, col_idx + it.dst, it.len, it.lo, it.bits);
+        sort_span(S, tmp + it.src, col_idx + it.dst, it.len, it.lo, it.range);
     }
 }
 
@@ -362,7 +399,7 @@ cudaError_t launch_sort_rows(const Plan &p, const QueryBufs &b, const int32_t co
         int32_t *ctr = (int32_t *)w;
         cudaMemsetAsync(hist, 0, sizeof(int32_t) * 2 * (size_t)nbk_sum, s);
         cudaMemsetAsync(ctr, 0, 2 * sizeof(int32_t), s);
-        k_big_setup<<<1, 1, 0, s>>>(b.rows[2], n_big, row_off, br);
+        k_big_setup<<<1, kSetupThreads, 0, s>>>(b.rows[2], n_big, row_off, br);
         dim3 g(n_big, 64);
         k_big_hist<<<g, 256, 0, s>>>(br, row_off, p.n, col_idx, hist);
         k_big_scan<<<n_big, 1024, 0, s>>>(br, row_off, p.n, hist, items, ctr, slow, ctr + 1);
