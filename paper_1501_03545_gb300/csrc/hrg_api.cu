@@ -361,6 +361,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     int64_t heavy_cap = std::max<int64_t>(1 << 16, n / 64);
     if (J.p_hub > 0 && (rc = ensure(ctx, hrg_ctx::W_CURSOR, sizeof(int32_t) * J.p_hub, &cursor))) return rc;
     b.cursor = (int32_t *)cursor;
+
     for (int attempt = 0;; ++attempt) {
         if ((rc = ensure(ctx, hrg_ctx::W_HEAVY, sizeof(int4) * heavy_cap, &heavy))) return rc;
         b.heavy = (int4 *)heavy;

@@ -153,11 +153,18 @@ __device__ __forceinline__ float lhs32(const PMS &q, const PMS &c, int64_t dA)
     // dA = hi 2^32 + lo with hi signed and lo unsigned; two 32-bit
     // conversions (the 64-bit one is an order of magnitude slower) and one
     // FMA give dA * pi / 2^64 to within 3 ulp
-    const int32_t hi = (int32_t)(dA >> 32);
-    const uint32_t lo = (uint32_t)dA;
+    // (split of |dA|, so that both directions of a pair round identically)
+    const uint64_t ad = dA < 0 ? (0ull - (uint64_t)dA) : (uint64_t)dA;
+    const uint32_t hi = (uint32_t)(ad >> 32);
+    const uint32_t lo = (uint32_t)ad;
     const float half = fmaf((float)hi, 7.3145904e-10f /* pi / 2^32 */, (float)lo * 1.7030608e-19f /* pi / 2^64 */);
     const float s = sin_taylor(half);
-    return fmaf(q.S * c.S, s * s, fmaf(q.P, c.M, c.P * q.M));
+    // operands in a fixed order (smaller id first) so that the decision on a
+    // pair is the same whichever endpoint asks
+    const bool sw = q.id > c.id;
+    const float aP = sw ? c.P : q.P, aM = sw ? c.M : q.M;
+    const float bP = sw ? q.P : c.P, bM = sw ? q.M : c.M;
+    return fmaf(q.S * c.S, s * s, fmaf(aP, bM, bP * aM));
 }
 
 // sin(x) for |x| <= 2^-4 by Taylor through x^9 (error < x^11/11! < 1e-20 |x|),
@@ -180,6 +187,11 @@ __device__ __forceinline__ double sin_small64(double x)
 // sees.  Relative error a few ulp, far inside the 1e-12 tie band.
 __device__ __forceinline__ bool edge64(double r1, double phi1, double r2, double phi2, double coshR)
 {
+    // fixed operand order: both endpoints of a pair get the same value
+    if (r1 > r2 || (r1 == r2 && phi1 > phi2)) {
+        const double tr = r1, tp = phi1;
+        r1 = r2; phi1 = phi2; r2 = tr; phi2 = tp;
+    }
     const double s = sin_small64(0.5 * (phi1 - phi2));
     const double v = cosh(r1 - r2) + 2.0 * sinh(r1) * sinh(r2) * (s * s);
     return v < coshR;
@@ -200,8 +212,11 @@ __device__ __forceinline__ PMS64 scaled_exps64(const Plan &p, double r, double p
 
 __device__ __forceinline__ bool edge_pms64(const Plan &p, const PMS64 &q, const PMS64 &c)
 {
-    const double s = sin_small64(0.5 * (q.phi - c.phi));
-    const double v = fma(q.S * c.S, s * s, fma(q.P, c.M, c.P * q.M));
+    // fixed operand order: both endpoints of a pair get the same value
+    const bool sw = q.P > c.P || (q.P == c.P && q.phi > c.phi);
+    const PMS64 &a = sw ? c : q, &b = sw ? q : c;
+    const double s = sin_small64(0.5 * (a.phi - b.phi));
+    const double v = fma(a.S * b.S, s * s, fma(a.P, b.M, b.P * a.M));
     return v < p.rhs64;
 }
 
