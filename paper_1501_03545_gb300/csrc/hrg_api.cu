@@ -101,7 +101,7 @@ struct hrg_ctx {
     // workspace slots
     enum { W_BANDCNT, W_GBUF, W_CNT, W_START, W_PERM, W_A, W_PMS, W_PMS64, W_DEG, W_STATS, W_LIST0, W_LIST1,
            W_LIST2, W_LISTCNT, W_BIGTOT, W_SCAN, W_TMP, W_BUCKET, W_OUT_R, W_OUT_PHI, W_OUT_OFF, W_OUT_COL,
-           W_HEAVY, W_CURSOR, W_COUNT };
+           W_HEAVY, W_CURSOR, W_SMALL, W_SMALLOFF, W_SMALLCUR, W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
     cudaEvent_t ev[10] = {};  // stage boundaries of the current job
@@ -361,6 +361,16 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     int64_t heavy_cap = std::max<int64_t>(1 << 16, n / 64);
     if (J.p_hub > 0 && (rc = ensure(ctx, hrg_ctx::W_CURSOR, sizeof(int32_t) * J.p_hub, &cursor))) return rc;
     b.cursor = (int32_t *)cursor;
+    // rim rows of up to 32 entries kept by the count pass (about 8 entries per vertex)
+    void *small = nullptr, *small_off = nullptr, *small_cur = nullptr;
+    const int64_t small_cap = std::min<int64_t>(8 * n + 1024, 0x7fff0000LL);
+    if ((rc = ensure(ctx, hrg_ctx::W_SMALL, sizeof(int32_t) * small_cap, &small))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_SMALLOFF, sizeof(int32_t) * n, &small_off))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_SMALLCUR, sizeof(unsigned long long), &small_cur))) return rc;
+    b.small = (int32_t *)small;
+    b.small_off = (int32_t *)small_off;
+    b.small_cursor = (unsigned long long *)small_cur;
+    b.small_cap = small_cap;
 
     for (int attempt = 0;; ++attempt) {
         if ((rc = ensure(ctx, hrg_ctx::W_HEAVY, sizeof(int4) * heavy_cap, &heavy))) return rc;
@@ -370,6 +380,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
         CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 4, st));
         CK(cudaMemsetAsync(bigtot, 0, sizeof(int64_t), st));
         CK(cudaMemsetAsync(deg, 0, sizeof(int32_t) * n, st));
+        CK(cudaMemsetAsync(small_cur, 0, sizeof(unsigned long long), st));
         CK(launch_count_hub(p, b, J.fp64, J.p_hub, st));
         CK(cudaEventRecord(ctx->ev[3], st));
         CK(launch_count_rim(p, b, J.fp64, st));

@@ -50,6 +50,10 @@ struct QueryBufs {
     int32_t heavy_cap;
     int32_t *cursor;          // [p_hub] write cursor of each hub row
     int32_t *col_out;         // CSR neighbour ids being written (write pass only)
+    int32_t *small;           // [small_cap] sorted rim rows of up to kRegRow entries kept by the count pass
+    int32_t *small_off;       // [n] by position: start of the kept row in small, -1 if not kept
+    unsigned long long *small_cursor;  // [1] bump allocator over small
+    int64_t small_cap;
 };
 
 constexpr int kHeavy = 4096;      // hub ranges longer than this are split into chunks for whole CTAs

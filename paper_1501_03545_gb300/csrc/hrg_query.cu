@@ -111,61 +111,132 @@ __device__ __forceinline__ void classify_row(const QueryBufs &b, int32_t id, int
     if (cls == 2) atomicAdd((unsigned long long *)b.big_total, (unsigned long long)d);
 }
 
+// Bitonic sorting network over v[0..N) with compile-time indices (the array
+// stays in registers); the pad value 0x7fffffff sorts to the end.
+template <int N>
+__device__ __forceinline__ void bitonic_regs(int32_t (&v)[kRegRow])
+{
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const int32_t a = v[i], c = v[l];
+                    if ((i & k) == 0) { v[i] = min(a, c); v[l] = max(a, c); }
+                    else { v[i] = max(a, c); v[l] = min(a, c); }
+                }
+            }
+}
+
 // ---------------------------------------------------------------------------
-// One query, one thread (rim bands).
+// One query, one thread (rim bands).  Rows of up to kRegRow entries are kept
+// sorted in registers.  The count pass stores such a row in the row buffer
+// (b.small) and records where (b.small_off[position]); the write pass then
+// copies it instead of traversing the query again.  Longer rows, and rows
+// that did not fit in the buffer, are traversed again by the write pass.
 // ---------------------------------------------------------------------------
 template <bool F64, bool WRITE>
-__device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, int32_t qp,
+__device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, int32_t qp, bool active,
                                              const int64_t *__restrict__ row_off, int32_t *__restrict__ col_idx,
                                              unsigned &n_cand, unsigned &n_re, unsigned &n_edge)
 {
-    const PMS q = b.pms[qp];
-    const uint64_t Aq = b.A[qp];
-    PMS64 q64{};
-    if (F64) q64 = b.pms64[qp];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    PMS q{};
     int64_t base = 0;
     int32_t deg = 0;
-    if (WRITE) {
-        base = row_off[q.id];
-        deg = b.deg[q.id];
+    int32_t stored = -1;
+    if (active) {
+        q = b.pms[qp];
+        if (WRITE) {
+            base = row_off[q.id];
+            deg = (int32_t)(row_off[q.id + 1] - base);
+            stored = b.small_off[qp];
+        }
+    }
+    if (WRITE && active && stored >= 0) {
+        // the count pass kept this row (unsorted): sort it in registers, store it
+        int32_t v[kRegRow];
+#pragma unroll
+        for (int k = 0; k < kRegRow; ++k) v[k] = k < deg ? b.small[stored + k] : 0x7fffffff;
+        if (deg > 16) bitonic_regs<32>(v);
+        else if (deg > 8) bitonic_regs<16>(v);
+        else if (deg > 4) bitonic_regs<8>(v);
+        else if (deg > 1) bitonic_regs<4>(v);
+#pragma unroll
+        for (int k = 0; k < kRegRow; ++k)
+            if (k < deg) col_idx[base + k] = v[k];
+        return;
     }
     int32_t buf[kRegRow];
     int32_t cnt = 0;
-    for (int j = 0; j < p.B; ++j) {
-        const Ranges rg = band_ranges(p, b.start, q, Aq, j);
-        for (int part = 0; part < 2; ++part) {
-            const int32_t s = part ? rg.s1 : rg.s0, e = part ? rg.e1 : rg.e0;
-            for (int32_t c = s; c < e; ++c) {
-                if (c == qp) continue;
-                const uint64_t Ac = __ldg(b.A + c);
-                if (rg.W != kFullCircle && !within(Aq, Ac, rg.W)) continue;
-                const PMS cc = b.pms[c];
-                if (decide_loaded<F64>(p, b, q, q64, Aq, Ac, cc, c, kFullCircle, n_cand, n_re)) {
-                    if (WRITE) {
-                        if (deg <= kRegRow) {
-                            if (cnt < deg) {  // insertion into the sorted register list
+    if (active) {
+        const uint64_t Aq = b.A[qp];
+        PMS64 q64{};
+        if (F64) q64 = b.pms64[qp];
+        for (int j = 0; j < p.B; ++j) {
+            const Ranges rg = band_ranges(p, b.start, q, Aq, j);
+            for (int part = 0; part < 2; ++part) {
+                const int32_t s = part ? rg.s1 : rg.s0, e = part ? rg.e1 : rg.e0;
+                for (int32_t c = s; c < e; ++c) {
+                    if (c == qp) continue;
+                    const uint64_t Ac = __ldg(b.A + c);
+                    if (rg.W != kFullCircle && !within(Aq, Ac, rg.W)) continue;
+                    const PMS cc = b.pms[c];
+                    if (decide_loaded<F64>(p, b, q, q64, Aq, Ac, cc, c, kFullCircle, n_cand, n_re)) {
+                        if (WRITE) {
+                            if (cnt < kRegRow) {  // insertion into the sorted list (rows not kept)
                                 int32_t k = cnt;
                                 while (k > 0 && buf[k - 1] > cc.id) { buf[k] = buf[k - 1]; --k; }
                                 buf[k] = cc.id;
                             }
-                        } else if (cnt < deg) {
-                            col_idx[base + cnt] = cc.id;
+                            if (deg > kRegRow && cnt < deg) col_idx[base + cnt] = cc.id;
+                        } else if (cnt < kRegRow) {
+                            buf[cnt] = cc.id;  // count pass: kept unsorted
                         }
+                        ++cnt;
                     }
-                    ++cnt;
                 }
             }
         }
     }
-    n_edge += cnt;
     if (WRITE) {
-        if (cnt != deg) atomicOr((unsigned long long *)&b.stats[ST_ERR], 1ull);
-        if (deg <= kRegRow)
-            for (int32_t k = 0; k < cnt && k < deg; ++k) col_idx[base + k] = buf[k];
+        if (active) {
+            if (cnt != deg) atomicOr((unsigned long long *)&b.stats[ST_ERR], 1ull);
+            if (deg <= kRegRow)
+                for (int32_t k = 0; k < cnt && k < deg; ++k) col_idx[base + k] = buf[k];
+        }
     } else {
-        b.deg[q.id] = cnt;
-        classify_row(b, q.id, cnt);
+        // keep rows of up to kRegRow entries: warp-aggregated reservation in b.small
+        const bool keep = active && cnt <= kRegRow && cnt > 0;
+        int32_t want = keep ? cnt : 0;
+        int32_t incl = want;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        long long wbase = 0;
+        if (lane == 31 && tot > 0) wbase = atomicAdd((unsigned long long *)b.small_cursor, (unsigned long long)tot);
+        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+        (void)lt;
+        if (active) {
+            const long long pos = wbase + incl - want;
+            int32_t off = -1;
+            if (keep && pos + cnt <= b.small_cap) {
+                for (int32_t k = 0; k < cnt; ++k) b.small[pos + k] = buf[k];
+                off = (int32_t)pos;
+            }
+            b.small_off[qp] = off;
+            b.deg[q.id] = cnt;
+            classify_row(b, q.id, cnt);
+        }
     }
+    if (active) n_edge += cnt;
 }
 
 // One CTA per angular sector: the queries of all rim bands whose angle lies
@@ -199,10 +270,16 @@ __global__ void __launch_bounds__(256) k_rim_sector(Plan p, QueryBufs b, const i
     const int32_t total = s_pre[HRG_MAX_BANDS];
     unsigned n_cand = 0, n_re = 0, n_edge = 0;
     int j = 0;
-    for (int32_t t = threadIdx.x; t < total; t += blockDim.x) {
-        while (t >= s_pre[j + 1]) ++j;  // t only grows, so j only moves forward
-        const int32_t qp = s_beg[j] + (t - s_pre[j]);
-        thread_query<F64, WRITE>(p, b, qp, row_off, col_idx, n_cand, n_re, n_edge);
+    // warp-uniform loop (the count pass reserves buffer space per warp)
+    for (int32_t t0 = threadIdx.x & ~31; t0 < total; t0 += blockDim.x) {
+        const int32_t t = t0 + (threadIdx.x & 31);
+        const bool active = t < total;
+        int32_t qp = 0;
+        if (active) {
+            while (t >= s_pre[j + 1]) ++j;  // t only grows, so j only moves forward
+            qp = s_beg[j] + (t - s_pre[j]);
+        }
+        thread_query<F64, WRITE>(p, b, qp, active, row_off, col_idx, n_cand, n_re, n_edge);
     }
     if (!WRITE) add_stats(b.stats, n_cand, n_re, n_edge);
 }
