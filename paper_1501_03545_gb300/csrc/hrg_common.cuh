@@ -236,13 +236,16 @@ __device__ __forceinline__ uint64_t window_halfwidth(const Plan &p, const PMS &q
     const float Pb = p.Pb[band], Mb = p.Mb[band], Sb = p.Sb[band];
     const float den = q.S * Sb;
     if (!(den > 0.0f)) return kFullCircle;
+    const float inv = __frcp_rn(den);
     const float sub = fmaf(q.P, Mb, Pb * q.M);
     const float num = p.rhs32 - sub;
-    float X = num / den;
-    X = X * (1.0f + 2e-5f) + 2e-5f * (1.0f + sub) / den;
+    // X = num / den, padded by 2e-5 relative and by the rounding of the difference
+    float X = fmaf(num, 1.0f + 2e-5f, 2e-5f * (1.0f + sub)) * inv;
     if (X >= 1.0f) return kFullCircle;
     if (!(X > 0.0f)) X = 0.0f;
-    float th = 2.0f * asinf(sqrtf(X));
+    // theta = 2 asin(sqrt X); for X <= 1/4 the bound asin(y) <= y / sqrt(1 - y^2)
+    // (asin y = atan(y / sqrt(1 - y^2))) avoids asinf at < 9% extra width
+    float th = X <= 0.25f ? 2.0f * sqrtf(X * __frcp_rn(1.0f - X)) : 2.0f * asinf(sqrtf(X));
     th = th * (1.0f + 2e-5f) + 1e-30f;
     if (th >= 3.1415f) return kFullCircle;
     return __float2ull_ru(th * kAngleScaleUp) + (1ull << 16);

@@ -34,27 +34,29 @@ struct Ranges { int32_t s0, e0, s1, e1; uint64_t W; };
 __device__ __forceinline__ Ranges band_ranges(const Plan &p, const int32_t *__restrict__ start, const PMS &q,
                                               uint64_t Aq, int j)
 {
+    // four table reads, always issued (no branch on their values), so the
+    // reads of several bands can be in flight together
     Ranges rg;
-    const int64_t b0 = p.base[j], b1 = p.base[j + 1];
-    const int32_t s = __ldg(start + b0), e = __ldg(start + b1);
-    rg.s1 = rg.e1 = 0;
-    rg.W = kFullCircle;
-    if (s == e) { rg.s0 = rg.e0 = 0; return rg; }
+    const int64_t b0 = p.base[j];
+    const int g = p.gbits[j];
+    const int64_t G = (int64_t)1 << g;  // buckets of band j
     const uint64_t W = window_halfwidth(p, q, j);
     rg.W = W;
-    const int g = p.gbits[j];
-    if (W == kFullCircle || g == 0) { rg.s0 = s; rg.e0 = e; return rg; }
-    const uint64_t lo = Aq - W, hi = Aq + W;
-    const int64_t blo = (int64_t)(lo >> (64 - g)), bhi = (int64_t)(hi >> (64 - g));
-    if (lo <= hi) {
-        rg.s0 = __ldg(start + b0 + blo);
-        rg.e0 = __ldg(start + b0 + bhi + 1);
-    } else {  // the window wraps through angle 0
-        rg.s0 = __ldg(start + b0 + blo);
-        rg.e0 = e;
-        rg.s1 = s;
-        rg.e1 = __ldg(start + b0 + bhi + 1);
+    int64_t i0 = 0, i1 = G, i2 = 0, i3 = 0;
+    if (W != kFullCircle && g != 0) {
+        const uint64_t lo = Aq - W, hi = Aq + W;
+        const int64_t bl = (int64_t)(lo >> (64 - g)), bh = (int64_t)(hi >> (64 - g));
+        i0 = bl;
+        if (lo <= hi) {
+            i1 = bh + 1;
+        } else {  // the window wraps through angle 0
+            i3 = bh + 1;
+        }
     }
+    rg.s0 = __ldg(start + b0 + i0);
+    rg.e0 = __ldg(start + b0 + i1);
+    rg.s1 = __ldg(start + b0 + i2);
+    rg.e1 = __ldg(start + b0 + i3);
     return rg;
 }
 
