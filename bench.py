@@ -146,6 +146,25 @@ def oracle_rate(n=ORACLE_SAMPLE_N):
             "seconds": dt}
 
 
+def replica_seed(w, rank):
+    """Seed of rank's graph: every rank generates an independent graph of the
+    same workload (no data-path collective; the path does not shard)."""
+    return w.seed + rank
+
+
+def reduce_over_ranks(ms, entries, dist, device):
+    """Whole-job timing: the slowest rank's timed milliseconds and the entries
+    all ranks produced.  dist is None on one process."""
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    e = torch.tensor([float(entries)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -202,7 +221,7 @@ def main():
 
     H.load()
     w = WORKLOAD if args.n <= 0 else W.scaled(WORKLOAD, args.n)
-    seed = w.seed + rank
+    seed = replica_seed(w, rank)
     ctx = H.Context(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
@@ -236,13 +255,8 @@ def main():
         barrier()
     ms = ev0.elapsed_time(ev1)
     clocks = clk.summary()
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    e = torch.tensor([float(entries)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    value = float(e.item()) / (ms_max / 1e3)
+    ms_max, total = reduce_over_ranks(ms, entries, dist, dev)
+    value = total / (ms_max / 1e3)
     last = stats[-1]
     n_entries = last["n_entries"]
 

@@ -57,6 +57,9 @@ typedef struct hrg_params {
     double R_override;  /* > 0: use this disk radius instead of solving Eq. (22)     */
     uint32_t flags;     /* HRG_FLAG_*                                                */
     int32_t bands;      /* 0: automatic; else number of radial bands (1..64)         */
+    int32_t hub_candidates; /* 0: automatic (512); vertices whose band's inner radius
+                               expects more candidates are queried one warp each     */
+    int32_t reserved;
 } hrg_params;
 
 typedef struct hrg_stats {

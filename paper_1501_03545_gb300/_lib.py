@@ -33,7 +33,7 @@ class HrgError(RuntimeError):
 class hrg_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("alpha", ctypes.c_double), ("avg_degree", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("R_override", ctypes.c_double), ("flags", ctypes.c_uint32),
-                ("bands", ctypes.c_int32)]
+                ("bands", ctypes.c_int32), ("hub_candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class hrg_stats(ctypes.Structure):
@@ -146,16 +146,17 @@ class Context:
             raise HrgError(rc, self.last_error())
 
 
-def params(n, alpha, avg_degree, seed, R_override=0.0, fp64_only=False, bands=0) -> hrg_params:
+def params(n, alpha, avg_degree, seed, R_override=0.0, fp64_only=False, bands=0, hub_candidates=0) -> hrg_params:
     return hrg_params(int(n), float(alpha), float(avg_degree), int(seed), float(R_override),
-                      HRG_FLAG_FP64_ONLY if fp64_only else 0, int(bands))
+                      HRG_FLAG_FP64_ONLY if fp64_only else 0, int(bands), int(hub_candidates), 0)
 
 
 def _dptr(t) -> int:
     return t.data_ptr()
 
 
-def generate(ctx: Context, n, alpha, avg_degree, seed, R_override=0.0, fp64_only=False, bands=0, stream=None):
+def generate(ctx: Context, n, alpha, avg_degree, seed, R_override=0.0, fp64_only=False, bands=0, stream=None,
+             hub_candidates=0):
     """Device generation through hrg_generate_begin / hrg_generate_finish.
     Returns dict of torch tensors (r, phi, row_off, col_idx) and stats."""
     import torch
@@ -166,7 +167,7 @@ def generate(ctx: Context, n, alpha, avg_degree, seed, R_override=0.0, fp64_only
     r = torch.empty(n, dtype=torch.float64, device=dev)
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     off = torch.empty(n + 1, dtype=torch.int64, device=dev)
-    p = params(n, alpha, avg_degree, seed, R_override, fp64_only, bands)
+    p = params(n, alpha, avg_degree, seed, R_override, fp64_only, bands, hub_candidates)
     job = _P()
     ne = ctypes.c_int64()
     ctx.check(L.hrg_generate_begin(ctx.h, ctypes.byref(p), _P(st.cuda_stream), _P(_dptr(r)), _P(_dptr(phi)),

@@ -215,7 +215,7 @@ static void plan_bands(Plan &p, int64_t n, double R, double alpha, int bands)
     p.alpha = alpha;
     p.big = std::cosh(alpha * R) - 1.0;
     p.half_R = 0.5 * R;
-    int B = bands > 0 ? bands : (int)std::ceil(R / 1.25);
+    int B = bands > 0 ? bands : (int)std::ceil(R / 1.5);
     if (B < 1) B = 1;
     if (B > HRG_MAX_BANDS) B = HRG_MAX_BANDS;
     p.B = B;
@@ -239,7 +239,7 @@ static void plan_bands(Plan &p, int64_t n, double R, double alpha, int bands)
 }
 
 // Angular buckets and hub bands once the band counts are known.
-static void plan_buckets(Plan &p, const int64_t *cnt, int32_t *p_hub)
+static void plan_buckets(Plan &p, const int64_t *cnt, int32_t *p_hub, double hub_cand)
 {
     // 2^sbits angular sectors of about 1024 points each; every band gets at
     // least one bucket per sector so sectors are bucket-aligned in each band
@@ -258,7 +258,7 @@ static void plan_buckets(Plan &p, const int64_t *cnt, int32_t *p_hub)
     p.base[p.B] = G;
     p.G = G;
     // hub bands: expected candidates of a query at the band's inner radius
-    // above ~512 (sum over bands of count * window / pi)
+    // above hub_cand (sum over bands of count * window / pi)
     int hub = 0;
     for (int i = 0; i < p.B; ++i) {
         const double rq = p.band_lo[i];
@@ -274,7 +274,7 @@ static void plan_buckets(Plan &p, const int64_t *cnt, int32_t *p_hub)
             }
             cand += frac * (double)cnt[j];
         }
-        if (cand > 512.0) hub = i + 1; else break;
+        if (cand > hub_cand) hub = i + 1; else break;
     }
     p.hub_bands = hub;
     int64_t ph = 0;
@@ -328,7 +328,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     CK(cudaStreamSynchronize(st));
     int64_t cnt_copy[HRG_MAX_BANDS];
     memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
-    plan_buckets(p, cnt_copy, &J.p_hub);
+    plan_buckets(p, cnt_copy, &J.p_hub, (prm && prm->hub_candidates > 0) ? (double)prm->hub_candidates : 512.0);
 
     // 2. counting sort by (band, angular bucket)
     void *cnt, *start;
