@@ -3,15 +3,18 @@
 // The query traversal emits a row's neighbours in (band, angle) order.  The
 // canonical CSR lists each row ascending, so rows longer than kRegRow (sorted
 // in registers by the query itself) are sorted here:
-//   * kRegRow < d <= kWarpRow:  one warp per row, bitonic sort in shared memory;
-//   * kWarpRow < d <= kSmemRow: one CTA per row, bucket sort in shared memory
-//     (the ids of a row are spread evenly over [0, n), so ~d/2 value buckets
-//     hold ~2 ids each);
+//   * kRegRow < d <= kWarpRow:  one warp per row, bucket sort in the warp's
+//     shared-memory slice (the ids of a row are spread evenly over [0, n), so
+//     d/4 .. d/2 equal-width value buckets hold 2..4 ids each);
+//   * kWarpRow < d <= kSmemRow: one CTA per row, the same bucket sort over
+//     the whole CTA;
 //   * d > kSmemRow: the row's ids are split by value into buckets of expected
 //     size <= 4096 (bucket k holds ids in [k n / nbk, (k+1) n / nbk)), every
 //     bucket is sorted by the CTA bucket sort; a bucket that still exceeds
 //     kSmemRow (only for id-clustered injected point sets) is sorted by a
 //     bitonic network in global memory.
+// Value buckets are taken as umulhi(key, mul) with mul = floor(nb 2^32 /
+// range): monotone in the key and below nb for every key < range.
 #include <cstdio>
 #include "hrg_internal.h"
 
@@ -21,90 +24,13 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kWarps = kSortThreads / 32;
+constexpr int kCtaThreads = 512;  // CTA bucket sort
+constexpr int kCtaWarps = kCtaThreads / 32;
 constexpr int kSetupThreads = 1024;  // k_big_setup needs whole warps (shuffle scans)
 
-// --------------------------------------------------------------------------
-// Warp bitonic sort of m (power of two) keys in shared memory.
-// --------------------------------------------------------------------------
-__device__ void warp_bitonic(int32_t *s, int m, int lane)
+__device__ __forceinline__ uint32_t bucket_mul(uint32_t nb, uint32_t range)
 {
-    for (int k = 2; k <= m; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = lane; i < m; i += 32) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const int32_t a = s[i], c = s[l];
-                    if ((a > c) == ((i & k) == 0)) { s[i] = c; s[l] = a; }
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ cnt,
-                                                            const int64_t *__restrict__ row_off, int32_t *__restrict__ col_idx)
-{
-    __shared__ int32_t sm[kWarps][kWarpRow];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * kWarps + w;
-    if (r >= *cnt) return;
-    const int32_t id = rows[r];
-    const int64_t base = row_off[id];
-    const int d = (int)(row_off[id + 1] - base);
-    int m = 32;
-    while (m < d) m <<= 1;
-    int32_t *s = sm[w];
-    for (int i = lane; i < m; i += 32) s[i] = i < d ? col_idx[base + i] : 0x7fffffff;
-    __syncwarp();
-    warp_bitonic(s, m, lane);
-    for (int i = lane; i < d; i += 32) col_idx[base + i] = s[i];
-}
-
-// --------------------------------------------------------------------------
-// CTA bucket sort of m <= kSmemRow keys in [lo, lo + range): the ids of a
-// row are spread evenly over their range, so ~m/2 equal-width buckets hold ~2
-// keys each.  Count (shared atomics), scan, scatter, then every bucket is
-// sorted on its own: by one thread (insertion) up to 32 keys, by one warp
-// (bitonic) beyond, so skewed inputs stay correct.
-// --------------------------------------------------------------------------
-constexpr int kMaxSortBuckets = 8192;
-
-struct SortSmem {
-    uint32_t tmp[kSmemRow];
-    uint32_t cnt[kMaxSortBuckets + 1];
-    uint32_t wsum[kWarps];
-};
-
-__device__ __forceinline__ uint32_t key_bucket(uint32_t k, uint32_t nb, uint32_t range)
-{
-    return (uint32_t)(((uint64_t)k * nb) / range);
-}
-
-// in-place exclusive scan of c[0..nb) (nb <= kMaxSortBuckets) by the whole CTA
-__device__ void cta_exclusive_scan(uint32_t *c, uint32_t nb, uint32_t *wsum)
-{
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const uint32_t per = (nb + kSortThreads - 1) / kSortThreads;
-    const uint32_t b0 = min(nb, t * per), b1 = min(nb, b0 + per);
-    uint32_t s = 0;
-    for (uint32_t i = b0; i < b1; ++i) s += c[i];
-    uint32_t inc = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) wsum[w] = inc;
-    __syncthreads();
-    if (t == 0) {
-        uint32_t acc = 0;
-        for (int k = 0; k < kWarps; ++k) { const uint32_t v = wsum[k]; wsum[k] = acc; acc += v; }
-    }
-    __syncthreads();
-    uint32_t run = inc - s + wsum[w];
-    for (uint32_t i = b0; i < b1; ++i) { const uint32_t v = c[i]; c[i] = run; run += v; }
-    __syncthreads();
+    return (uint32_t)(((uint64_t)nb << 32) / (uint64_t)range);
 }
 
 // warp bitonic sort of a[0..L) in shared memory, any L (positions >= L act as
@@ -127,51 +53,157 @@ __device__ void warp_bitonic_any(uint32_t *a, int L, int lane)
         }
 }
 
+// insertion sort of a[s0..e0) by one thread
+__device__ __forceinline__ void insertion(uint32_t *a, uint32_t s0, uint32_t e0)
+{
+    for (uint32_t i = s0 + 1; i < e0; ++i) {
+        const uint32_t v = a[i];
+        uint32_t k = i;
+        while (k > s0 && a[k - 1] > v) { a[k] = a[k - 1]; --k; }
+        a[k] = v;
+    }
+}
+
+// Buckets [cnt[b-1], cnt[b]) of b in [b_begin, nb) stepping by 32*stride warps:
+// up to 32 keys by the lane's own insertion sort, longer ones by the warp.
+__device__ void sort_buckets(uint32_t *key, const uint32_t *cnt, uint32_t nb, uint32_t b_begin, uint32_t b_step,
+                             int lane)
+{
+    for (uint32_t b0 = b_begin; b0 < nb; b0 += b_step) {
+        const uint32_t b = b0 + lane;
+        const uint32_t s0 = (b < nb && b) ? cnt[b - 1] : 0u, e0 = b < nb ? cnt[b] : 0u;
+        if (b < nb && e0 - s0 > 1 && e0 - s0 <= 32) insertion(key, s0, e0);
+        unsigned big = __ballot_sync(0xffffffffu, b < nb && e0 - s0 > 32);
+        __syncwarp();
+        while (big) {
+            const int src_lane = __ffs(big) - 1;
+            big &= big - 1;
+            const uint32_t bs = __shfl_sync(0xffffffffu, s0, src_lane), be = __shfl_sync(0xffffffffu, e0, src_lane);
+            warp_bitonic_any(key + bs, (int)(be - bs), lane);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Warp bucket sort of one row of kRegRow < d <= kWarpRow ids.
+// --------------------------------------------------------------------------
+constexpr int kWarpBuckets = kWarpRow / 4;
+
+struct WarpSortSmem {
+    uint32_t key[kWarpRow];
+    uint32_t cnt[kWarpBuckets + 1];
+};
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ cnt,
+                                                            int64_t n, const int64_t *__restrict__ row_off,
+                                                            int32_t *col_idx)
+{
+    __shared__ WarpSortSmem sm[kWarps];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * kWarps + w;
+    if (r >= *cnt) return;
+    WarpSortSmem &S = sm[w];
+    const int32_t id = rows[r];
+    const int64_t base = row_off[id];
+    const int d = (int)(row_off[id + 1] - base);
+    uint32_t nb = 1;
+    while (nb * 4 <= (uint32_t)d && nb < (uint32_t)kWarpBuckets) nb <<= 1;
+    const uint32_t mul = bucket_mul(nb, (uint32_t)n);
+    int32_t *row = col_idx + base;
+    for (uint32_t i = lane; i <= nb; i += 32) S.cnt[i] = 0;
+    __syncwarp();
+    for (int i = lane; i < d; i += 32) atomicAdd(&S.cnt[__umulhi((uint32_t)row[i], mul)], 1u);
+    __syncwarp();
+    {   // exclusive scan of cnt[0..nb): a run of nb/32 counters per lane
+        const uint32_t per = (nb + 31) >> 5;
+        const uint32_t b0 = min(nb, lane * per), b1 = min(nb, b0 + per);
+        uint32_t s = 0;
+        for (uint32_t i = b0; i < b1; ++i) s += S.cnt[i];
+        uint32_t inc = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        uint32_t run = inc - s;
+        for (uint32_t i = b0; i < b1; ++i) { const uint32_t v = S.cnt[i]; S.cnt[i] = run; run += v; }
+    }
+    __syncwarp();
+    for (int i = lane; i < d; i += 32) {
+        const uint32_t v = (uint32_t)row[i];
+        S.key[atomicAdd(&S.cnt[__umulhi(v, mul)], 1u)] = v;
+    }
+    __syncwarp();
+    sort_buckets(S.key, S.cnt, nb, 0, 32, lane);
+    __syncwarp();
+    for (int i = lane; i < d; i += 32) row[i] = (int32_t)S.key[i];
+}
+
+// --------------------------------------------------------------------------
+// CTA bucket sort of m <= kSmemRow keys in [lo, lo + range): the ids of a
+// row are spread evenly over their range, so ~m/2 equal-width buckets hold ~2
+// keys each.  Count (shared atomics), scan, scatter, then every bucket is
+// sorted on its own: by one thread (insertion) up to 32 keys, by one warp
+// (bitonic) beyond, so skewed inputs stay correct.
+// --------------------------------------------------------------------------
+constexpr int kMaxSortBuckets = 8192;
+
+struct SortSmem {
+    uint32_t tmp[kSmemRow];
+    uint32_t cnt[kMaxSortBuckets + 1];
+    uint32_t wsum[kCtaWarps];
+};
+
+// in-place exclusive scan of c[0..nb) (nb <= kMaxSortBuckets) by the whole CTA
+__device__ void cta_exclusive_scan(uint32_t *c, uint32_t nb, uint32_t *wsum)
+{
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t per = (nb + kCtaThreads - 1) / kCtaThreads;
+    const uint32_t b0 = min(nb, t * per), b1 = min(nb, b0 + per);
+    uint32_t s = 0;
+    for (uint32_t i = b0; i < b1; ++i) s += c[i];
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (t == 0) {
+        uint32_t acc = 0;
+        for (int k = 0; k < kCtaWarps; ++k) { const uint32_t v = wsum[k]; wsum[k] = acc; acc += v; }
+    }
+    __syncthreads();
+    uint32_t run = inc - s + wsum[w];
+    for (uint32_t i = b0; i < b1; ++i) { const uint32_t v = c[i]; c[i] = run; run += v; }
+    __syncthreads();
+}
+
 __device__ void sort_span(SortSmem &S, const int32_t *src, int32_t *dst, int m, int32_t lo, uint32_t range)
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     uint32_t nb = 1;
     while (nb * 4 <= (uint32_t)m && nb < kMaxSortBuckets) nb <<= 1;
     if (range == 0) range = 1;
-    for (uint32_t i = t; i <= nb; i += kSortThreads) S.cnt[i] = 0;
+    const uint32_t mul = bucket_mul(nb, range);
+    for (uint32_t i = t; i <= nb; i += kCtaThreads) S.cnt[i] = 0;
     __syncthreads();
-    for (int i = t; i < m; i += kSortThreads) atomicAdd(&S.cnt[key_bucket((uint32_t)(src[i] - lo), nb, range)], 1u);
+    for (int i = t; i < m; i += kCtaThreads) atomicAdd(&S.cnt[__umulhi((uint32_t)(src[i] - lo), mul)], 1u);
     __syncthreads();
     cta_exclusive_scan(S.cnt, nb, S.wsum);
-    for (int i = t; i < m; i += kSortThreads) {
+    for (int i = t; i < m; i += kCtaThreads) {
         const uint32_t k = (uint32_t)(src[i] - lo);
-        S.tmp[atomicAdd(&S.cnt[key_bucket(k, nb, range)], 1u)] = k;
+        S.tmp[atomicAdd(&S.cnt[__umulhi(k, mul)], 1u)] = k;
     }
     __syncthreads();
-    // bucket b now spans [cnt[b-1], cnt[b]) (cnt[-1] = 0)
-    for (uint32_t b = t; b < nb; b += kSortThreads) {
-        const uint32_t s0 = b ? S.cnt[b - 1] : 0u, e0 = S.cnt[b];
-        if (e0 - s0 > 1 && e0 - s0 <= 32) {
-            for (uint32_t i = s0 + 1; i < e0; ++i) {
-                const uint32_t v = S.tmp[i];
-                uint32_t k = i;
-                while (k > s0 && S.tmp[k - 1] > v) { S.tmp[k] = S.tmp[k - 1]; --k; }
-                S.tmp[k] = v;
-            }
-        }
-    }
-    for (uint32_t b0 = w * 32; b0 < nb; b0 += kWarps * 32) {
-        const uint32_t b = b0 + lane;
-        const uint32_t s0 = (b < nb && b) ? S.cnt[b - 1] : 0u, e0 = b < nb ? S.cnt[b] : 0u;
-        unsigned big = __ballot_sync(0xffffffffu, b < nb && e0 - s0 > 32);
-        while (big) {
-            const int src_lane = __ffs(big) - 1;
-            big &= big - 1;
-            const uint32_t bs = __shfl_sync(0xffffffffu, s0, src_lane), be = __shfl_sync(0xffffffffu, e0, src_lane);
-            warp_bitonic_any(S.tmp + bs, (int)(be - bs), lane);
-        }
-    }
+    sort_buckets(S.tmp, S.cnt, nb, (uint32_t)w * 32, kCtaWarps * 32, lane);
     __syncthreads();
-    for (int i = t; i < m; i += kSortThreads) dst[i] = (int32_t)S.tmp[i] + lo;
+    for (int i = t; i < m; i += kCtaThreads) dst[i] = (int32_t)S.tmp[i] + lo;
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_cta_rows(const int32_t *__restrict__ rows,
+__global__ void __launch_bounds__(kCtaThreads) k_sort_cta_rows(const int32_t *__restrict__ rows,
                                                                 const int32_t *__restrict__ cnt, int64_t n,
                                                                 const int64_t *__restrict__ row_off,
                                                                 int32_t *__restrict__ col_idx)
@@ -189,22 +221,25 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_cta_rows(const int32_t *_
 // --------------------------------------------------------------------------
 // Big rows.
 // --------------------------------------------------------------------------
-struct BigRow { int64_t tmp_off; int64_t hist_off; int32_t nbk; int32_t id; };
+struct BigRow { int64_t tmp_off; int64_t hist_off; int32_t nbk; int32_t id; int64_t ch_off; };
 struct Item { int64_t src; int64_t dst; int32_t len; int32_t lo; uint32_t range; int32_t pad; };
 
-// offsets of the big rows' ids (tmp) and bucket counters (hist): one CTA,
-// chunked prefix sums over the rows
+constexpr int kBigChunk = 4096;   // entries of a big row one CTA histograms / scatters
+constexpr int kBigSmemBk = 8192;  // id buckets a CTA aggregates in shared memory
+
+// offsets of the big rows' ids (tmp), bucket counters (hist) and chunks: one
+// CTA, chunked prefix sums over the rows
 __global__ void __launch_bounds__(kSetupThreads) k_big_setup(const int32_t *__restrict__ rows, int n_big,
                                                     const int64_t *__restrict__ row_off, BigRow *__restrict__ br)
 {
-    __shared__ long long s_t[32], s_h[32];
-    __shared__ long long carry_t, carry_h;
+    __shared__ long long s_t[32], s_h[32], s_c[32];
+    __shared__ long long carry_t, carry_h, carry_c;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    if (t == 0) { carry_t = 0; carry_h = 0; }
+    if (t == 0) { carry_t = 0; carry_h = 0; carry_c = 0; }
     __syncthreads();
     for (int k0 = 0; k0 < n_big; k0 += blockDim.x) {
         const int k = k0 + t;
-        long long d = 0, h = 0;
+        long long d = 0, h = 0, c = 0;
         int32_t id = 0, nbk = 0;
         if (k < n_big) {
             id = rows[k];
@@ -212,44 +247,84 @@ __global__ void __launch_bounds__(kSetupThreads) k_big_setup(const int32_t *__re
             nbk = 2;
             while ((long long)nbk * 4096 < d) nbk <<= 1;
             h = 2 * (long long)nbk;
+            c = (d + kBigChunk - 1) / kBigChunk;
         }
-        long long it = d, ih = h;
+        long long it = d, ih = h, ic = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const long long yt = __shfl_up_sync(0xffffffffu, it, o), yh = __shfl_up_sync(0xffffffffu, ih, o);
-            if (lane >= o) { it += yt; ih += yh; }
+            const long long yt = __shfl_up_sync(0xffffffffu, it, o), yh = __shfl_up_sync(0xffffffffu, ih, o),
+                            yc = __shfl_up_sync(0xffffffffu, ic, o);
+            if (lane >= o) { it += yt; ih += yh; ic += yc; }
         }
-        if (lane == 31) { s_t[w] = it; s_h[w] = ih; }
+        if (lane == 31) { s_t[w] = it; s_h[w] = ih; s_c[w] = ic; }
         __syncthreads();
         if (t == 0) {
-            long long at = carry_t, ah = carry_h;
+            long long at = carry_t, ah = carry_h, ac = carry_c;
             for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-                const long long vt = s_t[q], vh = s_h[q];
-                s_t[q] = at; s_h[q] = ah;
-                at += vt; ah += vh;
+                const long long vt = s_t[q], vh = s_h[q], vc = s_c[q];
+                s_t[q] = at; s_h[q] = ah; s_c[q] = ac;
+                at += vt; ah += vh; ac += vc;
             }
             carry_t = at;
             carry_h = ah;
+            carry_c = ac;
         }
         __syncthreads();
-        if (k < n_big) br[k] = BigRow{s_t[w] + it - d, s_h[w] + ih - h, nbk, id};
+        if (k < n_big) br[k] = BigRow{s_t[w] + it - d, s_h[w] + ih - h, nbk, id, s_c[w] + ic - c};
         __syncthreads();
     }
 }
 
-__device__ __forceinline__ int32_t big_bucket(int32_t v, int32_t nbk, int64_t n)
+// first key of id bucket i of a row with multiplier mul: the least v with
+// umulhi(v, mul) >= i, i.e. ceil(i 2^32 / mul)
+__device__ __forceinline__ int64_t bucket_lo(int64_t i, uint32_t mul)
 {
-    return (int32_t)(((int64_t)v * nbk) / n);
+    return (int64_t)((((uint64_t)i << 32) + mul - 1) / mul);
 }
 
-__global__ void k_big_hist(const BigRow *__restrict__ br, const int64_t *__restrict__ row_off, int64_t n,
-                           const int32_t *__restrict__ col_idx, int32_t *__restrict__ hist)
+// the chunk of this CTA: its row (binary search over the rows' chunk offsets)
+// and the entry range [c0, c1) inside the row
+__device__ __forceinline__ bool big_chunk(const BigRow *br, int n_big, const int64_t *row_off, BigRow &R,
+                                          int64_t &base, int64_t &c0, int64_t &c1)
 {
-    const BigRow R = br[blockIdx.x];
-    const int64_t base = row_off[R.id], len = row_off[R.id + 1] - base;
+    const int64_t c = blockIdx.x;
+    int lo = 0, hi = n_big;  // last row with ch_off <= c
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (br[mid].ch_off <= c) lo = mid; else hi = mid;
+    }
+    R = br[lo];
+    base = row_off[R.id];
+    const int64_t len = row_off[R.id + 1] - base;
+    c0 = (c - R.ch_off) * kBigChunk;
+    c1 = min(len, c0 + kBigChunk);
+    return c0 < len;
+}
+
+// Histogram of the id buckets of every big row, aggregated per chunk in
+// shared memory.
+__global__ void __launch_bounds__(256) k_big_hist(const BigRow *__restrict__ br, int n_big,
+                                                  const int64_t *__restrict__ row_off, int64_t n,
+                                                  const int32_t *__restrict__ col_idx, int32_t *__restrict__ hist)
+{
+    __shared__ uint32_t hs[kBigSmemBk];
+    BigRow R;
+    int64_t base, c0, c1;
+    if (!big_chunk(br, n_big, row_off, R, base, c0, c1)) return;
+    const uint32_t mul = bucket_mul((uint32_t)R.nbk, (uint32_t)n);
     int32_t *h = hist + R.hist_off;
-    for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.y * blockDim.x)
-        atomicAdd(&h[big_bucket(col_idx[base + i], R.nbk, n)], 1);
+    if (R.nbk > kBigSmemBk) {
+        for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x)
+            atomicAdd(&h[__umulhi((uint32_t)col_idx[base + i], mul)], 1);
+        return;
+    }
+    for (int i = threadIdx.x; i < R.nbk; i += blockDim.x) hs[i] = 0;
+    __syncthreads();
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x)
+        atomicAdd(&hs[__umulhi((uint32_t)col_idx[base + i], mul)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < R.nbk; i += blockDim.x)
+        if (hs[i]) atomicAdd(&h[i], (int32_t)hs[i]);
 }
 
 // exclusive scan of one row's bucket counts into its cursor half; one item per
@@ -264,6 +339,7 @@ __global__ void k_big_scan(const BigRow *__restrict__ br, const int64_t *__restr
     int32_t *h = hist + R.hist_off;
     int32_t *cur = h + R.nbk;
     const int64_t rbase = row_off[R.id];
+    const uint32_t mul = bucket_mul((uint32_t)R.nbk, (uint32_t)n);
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int32_t t0 = 0; t0 < R.nbk; t0 += blockDim.x) {
@@ -281,9 +357,8 @@ __global__ void k_big_scan(const BigRow *__restrict__ br, const int64_t *__restr
             const int32_t st = carry + buf[threadIdx.x] - v;
             cur[i] = st;
             if (v > 0) {
-                const int32_t lo = (int32_t)(((int64_t)i * n + R.nbk - 1) / R.nbk);
-                const int32_t hi = (int32_t)(((int64_t)(i + 1) * n + R.nbk - 1) / R.nbk);
-                Item it{R.tmp_off + st, rbase + st, v, lo, (uint32_t)(hi - lo), 0};
+                const int64_t lo = bucket_lo(i, mul), hi = min(n, bucket_lo(i + 1, mul));
+                Item it{R.tmp_off + st, rbase + st, v, (int32_t)lo, (uint32_t)(hi - lo), 0};
                 if (v <= kSmemRow) items[atomicAdd(n_items, 1)] = it;
                 else slow[atomicAdd(n_slow, 1)] = it;
             }
@@ -294,21 +369,45 @@ __global__ void k_big_scan(const BigRow *__restrict__ br, const int64_t *__restr
     }
 }
 
-__global__ void k_big_scatter(const BigRow *__restrict__ br, const int64_t *__restrict__ row_off, int64_t n,
-                              const int32_t *__restrict__ col_idx, int32_t *__restrict__ hist,
-                              int32_t *__restrict__ tmp)
+// Scatter of every big row's ids into its id buckets (tmp): a chunk reserves
+// its bucket ranges with one global atomic per non-empty bucket, then places
+// its ids with shared-memory atomics.
+__global__ void __launch_bounds__(256) k_big_scatter(const BigRow *__restrict__ br, int n_big,
+                                                     const int64_t *__restrict__ row_off, int64_t n,
+                                                     const int32_t *__restrict__ col_idx, int32_t *__restrict__ hist,
+                                                     int32_t *__restrict__ tmp)
 {
-    const BigRow R = br[blockIdx.x];
-    const int64_t base = row_off[R.id], len = row_off[R.id + 1] - base;
+    __shared__ uint32_t hs[kBigSmemBk];
+    BigRow R;
+    int64_t base, c0, c1;
+    if (!big_chunk(br, n_big, row_off, R, base, c0, c1)) return;
+    const uint32_t mul = bucket_mul((uint32_t)R.nbk, (uint32_t)n);
     int32_t *cur = hist + R.hist_off + R.nbk;
     int32_t *t = tmp + R.tmp_off;
-    for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.y * blockDim.x) {
+    if (R.nbk > kBigSmemBk) {
+        for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+            const int32_t v = col_idx[base + i];
+            t[atomicAdd(&cur[__umulhi((uint32_t)v, mul)], 1)] = v;
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < R.nbk; i += blockDim.x) hs[i] = 0;
+    __syncthreads();
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x)
+        atomicAdd(&hs[__umulhi((uint32_t)col_idx[base + i], mul)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < R.nbk; i += blockDim.x) {
+        const uint32_t c = hs[i];
+        if (c) hs[i] = (uint32_t)atomicAdd(&cur[i], (int32_t)c);
+    }
+    __syncthreads();
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
         const int32_t v = col_idx[base + i];
-        t[atomicAdd(&cur[big_bucket(v, R.nbk, n)], 1)] = v;
+        t[atomicAdd(&hs[__umulhi((uint32_t)v, mul)], 1u)] = v;
     }
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_items(const Item *__restrict__ items,
+__global__ void __launch_bounds__(kCtaThreads) k_sort_items(const Item *__restrict__ items,
                                                              const int32_t *__restrict__ n_items,
                                                              const int32_t *__restrict__ tmp,
                                                              int32_t *__restrict__ col_idx)
@@ -380,9 +479,9 @@ cudaError_t launch_sort_rows(const Plan &p, const QueryBufs &b, const int32_t co
     }
     if (counts[0] > 0)
         k_sort_warp<<<(unsigned)((counts[0] + kWarps - 1) / kWarps), kSortThreads, 0, s>>>(b.rows[0], b.list_cnt + 0,
-                                                                                        row_off, col_idx);
+                                                                                        p.n, row_off, col_idx);
     if (counts[1] > 0)
-        k_sort_cta_rows<<<(unsigned)counts[1], kSortThreads, sizeof(SortSmem), s>>>(b.rows[1], b.list_cnt + 1, p.n,
+        k_sort_cta_rows<<<(unsigned)counts[1], kCtaThreads, sizeof(SortSmem), s>>>(b.rows[1], b.list_cnt + 1, p.n,
                                                                                  row_off, col_idx);
     if (counts[2] > 0) {
         const int n_big = counts[2];
@@ -400,12 +499,13 @@ cudaError_t launch_sort_rows(const Plan &p, const QueryBufs &b, const int32_t co
         cudaMemsetAsync(hist, 0, sizeof(int32_t) * 2 * (size_t)nbk_sum, s);
         cudaMemsetAsync(ctr, 0, 2 * sizeof(int32_t), s);
         k_big_setup<<<1, kSetupThreads, 0, s>>>(b.rows[2], n_big, row_off, br);
-        dim3 g(n_big, 64);
-        k_big_hist<<<g, 256, 0, s>>>(br, row_off, p.n, col_idx, hist);
+        // chunks: sum over the rows of ceil(d / kBigChunk) <= big_total / kBigChunk + n_big
+        const unsigned gc = (unsigned)(big_total / kBigChunk + n_big);
+        k_big_hist<<<gc, 256, 0, s>>>(br, n_big, row_off, p.n, col_idx, hist);
         k_big_scan<<<n_big, 1024, 0, s>>>(br, row_off, p.n, hist, items, ctr, slow, ctr + 1);
-        k_big_scatter<<<g, 256, 0, s>>>(br, row_off, p.n, col_idx, hist, tmp);
+        k_big_scatter<<<gc, 256, 0, s>>>(br, n_big, row_off, p.n, col_idx, hist, tmp);
         const unsigned gi = (unsigned)std::min<int64_t>(nbk_sum, 152 * 8);
-        k_sort_items<<<gi, kSortThreads, sizeof(SortSmem), s>>>(items, ctr, tmp, col_idx);
+        k_sort_items<<<gi, kCtaThreads, sizeof(SortSmem), s>>>(items, ctr, tmp, col_idx);
         k_sort_slow<<<64, 1024, 0, s>>>(slow, ctr + 1, tmp, col_idx);
     }
     return cudaGetLastError();
