@@ -165,6 +165,65 @@ def reduce_over_ranks(ms, entries, dist, device):
     return float(t.item()), float(e.item())
 
 
+def run_serving(H, device, seconds, slots):
+    """Replays the serving workload's Poisson arrivals for `seconds` against
+    an hrg_server; latency = done - submit (server clock)."""
+    import queue
+
+    reqs = [q for q in W.serving_requests(int(W.SERVE_RATE * seconds * 1.5) + 16) if q[0] <= seconds]
+    srv = H.Server(device, slots=slots)
+    try:
+        # warm-up: grow every worker's resident workspace to the largest request size
+        big = max(reqs, key=lambda q: q[1])
+        warm = [srv.submit(big[1], big[2], big[3], big[4]) for _ in range(2 * slots)]
+        for t in warm:
+            srv.wait(t)
+            srv.release(t)
+        base = srv.counters()
+        todo = queue.Queue()
+        done = []
+        lock = threading.Lock()
+
+        def collect():
+            while True:
+                t = todo.get()
+                if t is None:
+                    return
+                res = srv.wait(t)
+                with lock:
+                    done.append((res.status, res.submit_s, res.done_s, res.n_entries, res.batch_size))
+                srv.release(t)
+
+        cs = [threading.Thread(target=collect) for _ in range(8)]
+        for c in cs:
+            c.start()
+        t0 = time.perf_counter()
+        for (at, n, a, k, sd) in reqs:
+            d = t0 + at - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            todo.put(srv.submit(n, a, k, sd))
+        for _ in cs:
+            todo.put(None)
+        for c in cs:
+            c.join()
+        c1 = srv.counters()
+    finally:
+        srv.close()
+    lat = sorted(1e3 * (d - s) for (_, s, d, _, _) in done)
+    span = max(d for (_, _, d, _, _) in done) - min(s for (_, s, _, _, _) in done)
+    ents = sum(e for (_, _, _, e, _) in done)
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+    return {"requests": len(done), "failed": sum(1 for x in done if x[0] != 0), "offered_rate_req_s": W.SERVE_RATE,
+            "arrival_seconds": seconds, "span_s": span, "p50_ms": q(0.50), "p99_ms": q(0.99),
+            "mean_ms": statistics.mean(lat), "throughput_entries_s": ents / span,
+            "throughput_req_s": len(done) / span, "entries": ents,
+            "mean_batch": (c1["batched_requests"] - base["batched_requests"]) / max(1, c1["batches"] - base["batches"]),
+            "max_running": c1["max_running"], "slots": slots,
+            "recipe": "Poisson arrivals at %g req/s, n log-uniform [1e3, 3e7], alpha U[0.55, 1.5], kbar U[4, 32], "
+                      "seed 10000 + index, numpy draw seed %d" % (W.SERVE_RATE, W.SERVE_DRAW_SEED)}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -197,6 +256,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-slots", type=int, default=2)
     ap.add_argument("--oracle-n", type=int, default=ORACLE_SAMPLE_N)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--n", type=int, default=0, help="profiling only: same alpha/kbar/seed at another n")
@@ -280,6 +342,50 @@ def main():
         fms = a.elapsed_time(b) / args.fp64_steps
         fp64 = {"value": n_entries / (fms / 1e3), "unit": UNIT, "ms_per_step": fms}
 
+    # the batched workload: 4096 small graphs per call, with the band width and
+    # hub threshold of each size class picked by the tuner (untimed), and with
+    # the defaults
+    batched = None
+    if args.batch_steps > 0:
+        from paper_1501_03545_gb300 import autotune
+
+        items = W.batch_items()
+        table = autotune.tune(ctx, items, stream=stream)
+        tuned = autotune.apply(items, table)
+
+        def time_batch(its):
+            g = H.generate_batch(ctx, its, stream=stream)
+            del g
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ent = 0
+            for _ in range(args.batch_steps):
+                g = H.generate_batch(ctx, its, stream=stream)
+                ent = g["stats"]["n_entries"]
+                nl = g["stats"]["launches"]
+                del g
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / args.batch_steps, ent, nl
+
+        bms, bent, bl = time_batch(tuned)
+        dms, _, _ = time_batch(items)
+        batched = {"graphs_per_s": len(items) / (bms / 1e3), "entries_per_s": bent / (bms / 1e3),
+                   "ms_per_batch": bms, "graphs": len(items), "sum_n": sum(it[0] for it in items),
+                   "entries_per_batch": bent, "launches_per_batch": bl,
+                   "untuned_ms_per_batch": dms,
+                   "tuned": {str(k): {"band_width": v[0], "hub_candidates": v[1]} for k, v in table.items()},
+                   "recipe": "n log-uniform [1e3, 1e5], alpha U[0.55, 1.5], kbar from {4, 8, 16, 32}, seeds "
+                             "1000..%d, parameters drawn with numpy seed %d" % (999 + len(items),
+                                                                                 W.BATCH_DRAW_SEED)}
+
+    # serving: Poisson arrivals of mixed requests, continuous batching
+    serving = None
+    if args.serve_seconds > 0 and rank == 0:
+        serving = run_serving(H, local, args.serve_seconds, args.serve_slots)
+
     # end to end through the host-buffer entry point (D2H of all outputs)
     e2e = None
     if args.e2e_steps > 0:
@@ -336,7 +442,7 @@ def main():
                            "path": "fp32 filter + fp64 recheck", "entries_per_step": n_entries,
                            "undirected_edges_per_s": value / 2,
                            "l2": "no flush: every step writes and reads >8 GB, far above the 126 MB L2"},
-                "fp64_plain": fp64, "stage_ms": stage, "e2e": e2e, "roofline": roof, "clocks": clocks,
+                "fp64_plain": fp64, "batched": batched, "serving": serving, "stage_ms": stage, "e2e": e2e, "roofline": roof, "clocks": clocks,
                 "cpu_baseline": cpu, "gpu_launches": last.get("launches", 0) * args.steps,
                 "job": {k: last[k] for k in ("R", "candidates", "rechecks", "bands", "hub_bands", "buckets",
                                              "hub_queries", "mid_rows", "big_rows", "mu")}}

@@ -43,7 +43,8 @@ enum {
     HRG_EOVERFLOW = 3, /* output larger than the caller's capacity / index type */
     HRG_ECUDA = 4,     /* a CUDA runtime error; message in hrg_last_error()  */
     HRG_ESTATE = 5,    /* call out of order (e.g. finish without begin)      */
-    HRG_EINTERNAL = 6  /* a device-side consistency check failed             */
+    HRG_EINTERNAL = 6, /* a device-side consistency check failed             */
+    HRG_ETIMEOUT = 7   /* hrg_server_wait: the request is not done yet       */
 };
 
 /* Flags of hrg_params.flags */
@@ -139,6 +140,33 @@ int hrg_generate_from_points_begin(hrg_ctx *ctx, int64_t n, double R, const doub
                                    hrg_job **job, int64_t *n_entries);
 
 /*
+ * hrg_generate_batch_begin -- as hrg_generate_begin for `count` independent
+ * graphs generated together: every stage runs once over all of them (one
+ * kernel launch per stage for the whole batch), so thousands of small graphs
+ * cost about as much as one graph of their total size.
+ *   count        1 <= count <= 2^24
+ *   items        host hrg_params[count]; each item as in hrg_generate_begin
+ *                (its flags are ignored: the batch's `flags` apply to all)
+ *   r_out, phi_out   device double[N], N = sum of items[g].n (< 2^31)
+ *   row_off_out  device int64[N+1]
+ * Layout: graph g owns positions [off_g, off_g + n_g) of r_out, phi_out and
+ * the rows [off_g, off_g + n_g) of one concatenated CSR, off_g = n_0 + ... +
+ * n_{g-1}.  Its vertex i is Philox counter i under key items[g].seed (the
+ * points equal those of a single-graph call with the same parameters), and
+ * its rows hold LOCAL vertex ids in [0, n_g), ascending; row_off is global
+ * (graph g's entries are col_idx[row_off[off_g] .. row_off[off_g + n_g])).
+ * The band layout of each graph is planned from its expected band counts
+ * (Eq. (1)), so it can differ from a single-graph call's; the graph cannot.
+ * Finish with hrg_generate_finish; hrg_job_stats then reports totals
+ * (R, bands and mu of graph 0).
+ * Errors: as hrg_generate_begin; an invalid item returns HRG_EINVAL naming
+ * the item in hrg_last_error().
+ */
+int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_params *items, uint32_t flags, void *stream,
+                             double *r_out, double *phi_out, int64_t *row_off_out, hrg_job **job,
+                             int64_t *n_entries);
+
+/*
  * hrg_generate_finish -- the edge insertion of Algorithm 1: writes the
  * neighbour ids of every vertex into col_idx_out (device int32[n_entries],
  * caller owned) at the offsets produced by begin, each row ascending.
@@ -199,6 +227,74 @@ int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_host, double 
  * lookup or launch failed).  Calls no cudaMalloc/cudaFree.
  */
 int hrg_row_offsets_noalloc(const int32_t *deg, int64_t n, int64_t *row_off, void *stream);
+
+/*
+ * Request server -- generation requests of different sizes and parameters on
+ * one GPU with continuous batching.  The paper has no serving layer; this is
+ * the request loop around Algorithm 1 for callers that submit many graphs.
+ *
+ * hrg_server_create starts `slots` worker threads (1..64), each with its own
+ * context (whose workspace, band structures included, stays resident across
+ * requests) and stream.  A free worker admits the queued requests in arrival
+ * order while their estimated device bytes (outputs plus transient workspace)
+ * fit in mem_budget_bytes (<= 0: 70 % of the device's free memory at create),
+ * and generates them together as one batch (hrg_generate_batch_begin);
+ * requests arriving meanwhile join the next batch.  Batches of different
+ * workers run concurrently on the device.  Results do not depend on the
+ * batching: each equals hrg_generate of the same parameters.
+ * Errors: HRG_EINVAL (bad slots / out), HRG_ECUDA (device, memory query).
+ */
+typedef struct hrg_server hrg_server;
+
+typedef struct hrg_result {
+    int32_t status;         /* HRG_OK or the batch's error code                     */
+    int32_t batch_size;     /* requests generated together with this one           */
+    int64_t n;              /* vertices                                            */
+    int64_t n_entries;      /* 2m                                                  */
+    /* device pointers owned by the server until hrg_server_release:
+     * r[n], phi[n] in vertex-id order; row_off[n+1]; the neighbour ids of
+     * vertex i are col_idx[row_off[i] .. row_off[i+1]) (row_off[0] is in general
+     * not 0: col_idx is shared with the other requests of the batch), local
+     * ids in [0, n), ascending */
+    const double *r, *phi;
+    const int64_t *row_off;
+    const int32_t *col_idx;
+    /* seconds since hrg_server_create: submitted, admitted to a batch, done */
+    double submit_s, start_s, done_s;
+} hrg_result;
+
+typedef struct hrg_server_counters {
+    int64_t completed;         /* requests finished (any status)              */
+    int64_t batches;           /* batches generated                           */
+    int64_t batched_requests;  /* requests over all batches                   */
+    int64_t queued;            /* requests waiting for admission               */
+    int64_t max_running;       /* most batches in flight at once              */
+    int64_t in_use_bytes;      /* estimated device bytes admitted, unreleased  */
+    int64_t peak_in_use_bytes; /* maximum of in_use_bytes                     */
+    int64_t budget_bytes;
+} hrg_server_counters;
+
+int hrg_server_create(hrg_server **out, int device, int32_t slots, int64_t mem_budget_bytes);
+
+/* Queue a request (parameters as hrg_generate_begin; flags ignored).
+ * Errors: HRG_EINVAL (invalid parameters, no radius), HRG_ENOMEM (the
+ * request alone exceeds the memory budget). */
+int hrg_server_submit(hrg_server *s, const hrg_params *p, int64_t *ticket);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a request; fills *out and
+ * returns its status, or HRG_ETIMEOUT.  HRG_EINVAL for an unknown ticket. */
+int hrg_server_wait(hrg_server *s, int64_t ticket, double timeout_s, hrg_result *out);
+
+/* Give a finished request's device buffers back (they are freed when every
+ * request of the batch has been released).  HRG_ESTATE if not finished. */
+int hrg_server_release(hrg_server *s, int64_t ticket);
+
+int hrg_server_stats(hrg_server *s, hrg_server_counters *out);
+const char *hrg_server_last_error(hrg_server *s);
+
+/* Cancels queued requests (status HRG_ESTATE), waits for running batches,
+ * frees every result not yet released and the workers' contexts. */
+int hrg_server_destroy(hrg_server *s);
 
 /* Message of the last error on this context (never null). */
 const char *hrg_last_error(const hrg_ctx *ctx);

@@ -13,7 +13,7 @@ import threading
 
 from . import build as _build
 
-HRG_OK, HRG_EINVAL, HRG_ENOMEM, HRG_EOVERFLOW, HRG_ECUDA, HRG_ESTATE, HRG_EINTERNAL = range(7)
+HRG_OK, HRG_EINVAL, HRG_ENOMEM, HRG_EOVERFLOW, HRG_ECUDA, HRG_ESTATE, HRG_EINTERNAL, HRG_ETIMEOUT = range(8)
 HRG_FLAG_FP64_ONLY = 0x1
 
 # every symbol declared in include/hrg.h
@@ -21,6 +21,8 @@ EXPORTS = (
     "hrg_solve_radius", "hrg_expected_degree", "hrg_create", "hrg_destroy", "hrg_generate_begin",
     "hrg_generate_from_points_begin", "hrg_generate_finish", "hrg_job_stats", "hrg_job_release",
     "hrg_generate", "hrg_generate_host", "hrg_last_error", "hrg_version", "hrg_row_offsets_noalloc",
+    "hrg_generate_batch_begin", "hrg_server_create", "hrg_server_submit", "hrg_server_wait", "hrg_server_release",
+    "hrg_server_stats", "hrg_server_last_error", "hrg_server_destroy",
 )
 
 
@@ -93,10 +95,32 @@ def load(build_if_missing: bool = True):
         L.hrg_last_error.restype = ctypes.c_char_p
         L.hrg_version.restype = ctypes.c_char_p
         L.hrg_row_offsets_noalloc.argtypes = [_P, _I64, _P, _P]
+        L.hrg_generate_batch_begin.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(hrg_params), ctypes.c_uint32, _P,
+                                               _P, _P, _P, ctypes.POINTER(_P), _PI64]
+        L.hrg_server_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int32, _I64]
+        L.hrg_server_submit.argtypes = [_P, ctypes.POINTER(hrg_params), _PI64]
+        L.hrg_server_wait.argtypes = [_P, _I64, ctypes.c_double, ctypes.POINTER(hrg_result)]
+        L.hrg_server_release.argtypes = [_P, _I64]
+        L.hrg_server_stats.argtypes = [_P, ctypes.POINTER(hrg_server_counters)]
+        L.hrg_server_last_error.argtypes = [_P]
+        L.hrg_server_last_error.restype = ctypes.c_char_p
+        L.hrg_server_destroy.argtypes = [_P]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         _lib = L
         return L
+
+
+class hrg_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batch_size", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("n_entries", ctypes.c_int64), ("r", ctypes.c_void_p), ("phi", ctypes.c_void_p),
+                ("row_off", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("submit_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+class hrg_server_counters(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("completed", "batches", "batched_requests", "queued", "max_running",
+                                               "in_use_bytes", "peak_in_use_bytes", "budget_bytes")]
 
 
 def hrg_solve_radius(n: int, alpha: float, avg_degree: float) -> float:
@@ -182,6 +206,45 @@ def generate(ctx: Context, n, alpha, avg_degree, seed, R_override=0.0, fp64_only
     return {"r": r, "phi": phi, "row_off": off, "col_idx": col[: ne.value], "stats": s.as_dict()}
 
 
+def generate_batch(ctx: Context, items, fp64_only=False, stream=None):
+    """hrg_generate_batch_begin + hrg_generate_finish: items is a sequence of
+    (n, alpha, avg_degree, seed) or dicts with those keys (plus optional
+    R_override, bands, hub_candidates).  Returns the concatenated outputs
+    (r, phi, row_off global, col_idx with local ids), the graph offsets
+    goff[count+1] (host list) and stats."""
+    import torch
+
+    L = load()
+    dev = torch.device("cuda", ctx.device)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    arr = (hrg_params * len(items))()
+    goff = [0]
+    for k, it in enumerate(items):
+        if isinstance(it, dict):
+            arr[k] = params(it["n"], it["alpha"], it["avg_degree"], it["seed"], it.get("R_override", 0.0), False,
+                            it.get("bands", 0), it.get("hub_candidates", 0))
+        else:
+            arr[k] = params(*it)
+        goff.append(goff[-1] + int(arr[k].n))
+    N = goff[-1]
+    r = torch.empty(N, dtype=torch.float64, device=dev)
+    phi = torch.empty(N, dtype=torch.float64, device=dev)
+    off = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    job = _P()
+    ne = ctypes.c_int64()
+    ctx.check(L.hrg_generate_batch_begin(ctx.h, len(items), arr, HRG_FLAG_FP64_ONLY if fp64_only else 0,
+                                         _P(st.cuda_stream), _P(_dptr(r)), _P(_dptr(phi)), _P(_dptr(off)),
+                                         ctypes.byref(job), ctypes.byref(ne)))
+    try:
+        col = torch.empty(max(ne.value, 1), dtype=torch.int32, device=dev)
+        ctx.check(L.hrg_generate_finish(job, _P(_dptr(col))))
+        s = hrg_stats()
+        L.hrg_job_stats(job, ctypes.byref(s))
+    finally:
+        L.hrg_job_release(job)
+    return {"r": r, "phi": phi, "row_off": off, "col_idx": col[: ne.value], "goff": goff, "stats": s.as_dict()}
+
+
 def generate_from_points(ctx: Context, r, phi, R, fp64_only=False, bands=0, stream=None):
     """hrg_generate_from_points_begin + finish on caller device tensors r, phi."""
     import torch
@@ -232,3 +295,106 @@ def hrg_row_offsets_noalloc(deg, row_off, stream=None) -> int:
     st = stream if stream is not None else torch.cuda.current_stream(deg.device)
     return int(load().hrg_row_offsets_noalloc(_P(deg.data_ptr()), int(deg.numel()), _P(row_off.data_ptr()),
                                               _P(st.cuda_stream)))
+
+
+class Server:
+    """hrg_server: queued generation requests with continuous batching."""
+
+    def __init__(self, device: int = 0, slots: int = 2, mem_budget_bytes: int = 0):
+        L = load()
+        h = _P()
+        rc = L.hrg_server_create(ctypes.byref(h), int(device), int(slots), int(mem_budget_bytes))
+        if rc != HRG_OK:
+            raise HrgError(rc, "hrg_server_create failed")
+        self.h = h
+        self.device = device
+
+    def submit(self, n, alpha, avg_degree, seed, bands=0, hub_candidates=0) -> int:
+        p = params(n, alpha, avg_degree, seed, 0.0, False, bands, hub_candidates)
+        t = ctypes.c_int64()
+        rc = load().hrg_server_submit(self.h, ctypes.byref(p), ctypes.byref(t))
+        if rc != HRG_OK:
+            raise HrgError(rc, self.last_error())
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = -1.0) -> hrg_result:
+        """Blocks (GIL released) until the request is done; returns the
+        hrg_result (status may be non-zero) or raises on HRG_ETIMEOUT."""
+        res = hrg_result()
+        rc = load().hrg_server_wait(self.h, int(ticket), float(timeout_s), ctypes.byref(res))
+        if rc == HRG_ETIMEOUT:
+            raise TimeoutError("request %d not done" % ticket)
+        if rc == HRG_EINVAL and res.n == 0:
+            raise HrgError(rc, "unknown ticket %d" % ticket)
+        return res
+
+    def fetch(self, res: hrg_result):
+        """Host copies (numpy) of a finished request: r, phi, row_off
+        (rebased to 0), col_idx."""
+        import numpy as np
+        import torch
+
+        n, ne = int(res.n), int(res.n_entries)
+        dev = torch.device("cuda", self.device)
+        torch.cuda.synchronize(dev)
+        r = np.empty(n, dtype=np.float64)
+        phi = np.empty(n, dtype=np.float64)
+        off = np.empty(n + 1, dtype=np.int64)
+        _memcpy_d2h(r, res.r)
+        _memcpy_d2h(phi, res.phi)
+        _memcpy_d2h(off, res.row_off)
+        col = np.empty(ne, dtype=np.int32)
+        if ne:
+            _memcpy_d2h(col, res.col_idx + 4 * int(off[0]))
+        return r, phi, off - off[0], col
+
+    def release(self, ticket: int):
+        rc = load().hrg_server_release(self.h, int(ticket))
+        if rc != HRG_OK:
+            raise HrgError(rc, "release of %d failed" % ticket)
+
+    def counters(self) -> dict:
+        c = hrg_server_counters()
+        load().hrg_server_stats(self.h, ctypes.byref(c))
+        return {k: getattr(c, k) for k, _ in c._fields_}
+
+    def last_error(self) -> str:
+        return load().hrg_server_last_error(self.h).decode()
+
+    def close(self):
+        if self.h:
+            load().hrg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _memcpy_d2h(arr, dptr):
+    """Device-to-host copy into a numpy array through the CUDA runtime."""
+    rt = _cudart()
+    rc = rt.cudaMemcpy(ctypes.c_void_p(arr.ctypes.data), ctypes.c_void_p(dptr), ctypes.c_size_t(arr.nbytes), 2)
+    if rc != 0:
+        raise HrgError(HRG_ECUDA, "cudaMemcpy failed (%d)" % rc)
+
+
+_rt = None
+
+
+def _cudart():
+    global _rt
+    if _rt is None:
+        import torch  # noqa: F401  (loads the CUDA runtime the library links)
+
+        for name in ("libcudart.so.13", "libcudart.so.12", "libcudart.so"):
+            try:
+                _rt = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if _rt is None:
+            raise HrgError(HRG_ECUDA, "CUDA runtime library not found")
+    return _rt

@@ -93,19 +93,24 @@ struct hrg_job {
     int64_t *row_off = nullptr;
     cudaStream_t stream = nullptr;
     QueryBufs qb{};
+    int32_t batch = 0;       // graphs of a batch job (0: a single graph)
+    int64_t batch_G = 0;     // buckets over all graphs of a batch
 };
 
 struct hrg_ctx {
     int device = 0;
     std::string err;
     // workspace slots
-    enum { W_BANDCNT, W_GBUF, W_CNT, W_START, W_PERM, W_A, W_PMS, W_PMS64, W_DEG, W_STATS, W_LIST0, W_LIST1,
+    enum { W_BANDCNT, W_GBUF, W_CNT, W_START, W_SLOT, W_A, W_PMS, W_PMS64, W_DEG, W_STATS, W_LIST0, W_LIST1,
            W_LIST2, W_LISTCNT, W_BIGTOT, W_SCAN, W_TMP, W_BUCKET, W_OUT_R, W_OUT_PHI, W_OUT_OFF, W_OUT_COL,
-           W_HEAVY, W_CURSOR, W_SMALL, W_SMALLOFF, W_SMALLCUR, W_COUNT };
+           W_HEAVY, W_CURSOR, W_SMALL, W_SMALLOFF, W_SMALLCUR, W_PLANS, W_NOFF, W_SOFF, W_GRAPHOF, W_HUBCNT,
+           W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_KEPT, W_RELIST, W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
     cudaEvent_t ev[10] = {};  // stage boundaries of the current job
     hrg_job job;
+    std::vector<Plan> batch_plans;  // host plans of the current batch
+    std::vector<int64_t> batch_noff, batch_soff;
 };
 
 static int set_err(hrg_ctx *c, int code, const char *fmt, ...)
@@ -214,6 +219,7 @@ static void plan_bands(Plan &p, int64_t n, double R, double alpha, int bands)
     p.coshR = std::cosh(R);
     p.alpha = alpha;
     p.big = std::cosh(alpha * R) - 1.0;
+    p.inv_alpha = 1.0 / alpha;
     p.half_R = 0.5 * R;
     int B = bands > 0 ? bands : (int)std::ceil(R / 1.5);
     if (B < 1) B = 1;
@@ -282,85 +288,44 @@ static void plan_buckets(Plan &p, const int64_t *cnt, int32_t *p_hub, double hub
     *p_hub = (int32_t)ph;
 }
 
-static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params *prm, int64_t n, double R,
-                        double alpha, const double *r_in, const double *phi_in, double *r_out, double *phi_out,
-                        uint32_t flags, int32_t bands, cudaStream_t st, int64_t *row_off_out, int64_t *n_entries)
+// Degree count and row offsets over the structure in J.qb (A, pms, pms64,
+// start and, for batches, the batch tables already set): positions and
+// global ids [0, n).
+static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t st, int64_t *row_off_out,
+                             int64_t *n_entries)
 {
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
-    J = hrg_job();
-    J.ctx = ctx;
-    J.stream = st;
-    J.fp64 = (flags & HRG_FLAG_FP64_ONLY) != 0 || R > 80.0;
-    J.row_off = row_off_out;
-    Plan &p = J.plan;
-    plan_bands(p, n, R, alpha, bands);
-
-    void *band_cnt, *gbuf, *perm, *A, *pms, *pms64 = nullptr, *deg, *stats, *lists[3], *listcnt, *bigtot, *scanws;
+    QueryBufs &b = J.qb;
+    void *deg, *stats, *lists[3], *listcnt, *bigtot, *scanws;
     int rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_BANDCNT, sizeof(int64_t) * HRG_MAX_BANDS, &band_cnt))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_GBUF, sizeof(int32_t) * n, &gbuf))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_PERM, sizeof(int32_t) * n, &perm))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_A, sizeof(uint64_t) * n, &A))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_PMS, sizeof(PMS) * n, &pms))) return rc;
-    if (J.fp64 && (rc = ensure(ctx, hrg_ctx::W_PMS64, sizeof(PMS64) * n, &pms64))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_DEG, sizeof(int32_t) * n, &deg))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_STATS, sizeof(uint64_t) * 8, &stats))) return rc;
     for (int k = 0; k < 3; ++k)
         if ((rc = ensure(ctx, hrg_ctx::W_LIST0 + k, sizeof(int32_t) * n, &lists[k]))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 4, &listcnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 8, &listcnt))) return rc;
+    void *kept, *relist;
+    if ((rc = ensure(ctx, hrg_ctx::W_KEPT, sizeof(int32_t) * n, &kept))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_RELIST, sizeof(int32_t) * n, &relist))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_BIGTOT, sizeof(int64_t), &bigtot))) return rc;
-
-    // 1. points and band counts
-    CK(cudaEventRecord(ctx->ev[0], st));
-    CK(cudaMemsetAsync(band_cnt, 0, sizeof(int64_t) * HRG_MAX_BANDS, st));
-    if (sampled) {
-        CK(launch_sample(p, prm->seed, r_out, phi_out, (int64_t *)band_cnt, st));
-        J.r = r_out;
-        J.phi = phi_out;
-    } else {
-        CK(launch_count_bands(p, r_in, phi_in, (int64_t *)band_cnt, st));
-        J.r = r_in;
-        J.phi = phi_in;
-    }
-    CK(cudaEventRecord(ctx->ev[1], st));
-    int64_t *h_cnt = (int64_t *)ctx->pinned;
-    CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    int64_t cnt_copy[HRG_MAX_BANDS];
-    memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
-    plan_buckets(p, cnt_copy, &J.p_hub, (prm && prm->hub_candidates > 0) ? (double)prm->hub_candidates : 512.0);
-
-    // 2. counting sort by (band, angular bucket)
-    void *cnt, *start;
-    const size_t scan_bytes = std::max(scan_workspace_bytes(p.G), scan_workspace_bytes(n));
-    if ((rc = ensure(ctx, hrg_ctx::W_CNT, sizeof(int32_t) * p.G, &cnt))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_START, sizeof(int32_t) * (p.G + 1), &start))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_bytes, &scanws))) return rc;
-    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * p.G, st));
-    CK(launch_bucket_hist(p, J.r, J.phi, (int32_t *)gbuf, (int32_t *)cnt, st));
-    CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, p.G, scanws, st));
-    CK(launch_bucket_scatter(p, (int32_t *)gbuf, (int32_t *)start, (int32_t *)cnt, (int32_t *)perm, st));
-    CK(launch_build_soa(p, (int32_t *)perm, J.r, J.phi, (uint64_t *)A, (PMS *)pms, (PMS64 *)pms64, st));
-    CK(cudaEventRecord(ctx->ev[2], st));
-
-    // 3. degrees
-    QueryBufs &b = J.qb;
-    b.A = (uint64_t *)A;
-    b.pms = (PMS *)pms;
-    b.pms64 = (PMS64 *)pms64;
-    b.start = (int32_t *)start;
+    if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_workspace_bytes(n), &scanws))) return rc;
+    const Plan &p = J.plan;
     b.r = J.r;
     b.phi = J.phi;
     b.deg = (int32_t *)deg;
     b.stats = (unsigned long long *)stats;
     for (int k = 0; k < 3; ++k) b.rows[k] = (int32_t *)lists[k];
     b.list_cnt = (int32_t *)listcnt;
+    b.kept = (int32_t *)kept;
+    b.relist = (int32_t *)relist;
     b.big_total = (int64_t *)bigtot;
     // heavy hub segments (long hub ranges cut into CTA chunks) and hub row cursors
-    void *heavy = nullptr, *cursor = nullptr;
+    void *heavy = nullptr, *cursor = nullptr, *wcnt = nullptr, *scnt = nullptr;
     int64_t heavy_cap = std::max<int64_t>(1 << 16, n / 64);
-    if (J.p_hub > 0 && (rc = ensure(ctx, hrg_ctx::W_CURSOR, sizeof(int32_t) * J.p_hub, &cursor))) return rc;
+    if (J.p_hub > 0) {
+        if ((rc = ensure(ctx, hrg_ctx::W_CURSOR, sizeof(int32_t) * J.p_hub, &cursor))) return rc;
+        if ((rc = ensure(ctx, hrg_ctx::W_WARPCNT, sizeof(int32_t) * J.p_hub, &wcnt))) return rc;
+    }
     b.cursor = (int32_t *)cursor;
+    b.warp_cnt = (int32_t *)wcnt;
     // rim rows of up to 32 entries kept by the count pass (about 8 entries per vertex)
     void *small = nullptr, *small_off = nullptr, *small_cur = nullptr;
     const int64_t small_cap = std::min<int64_t>(8 * n + 1024, 0x7fff0000LL);
@@ -374,10 +339,12 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
 
     for (int attempt = 0;; ++attempt) {
         if ((rc = ensure(ctx, hrg_ctx::W_HEAVY, sizeof(int4) * heavy_cap, &heavy))) return rc;
+        if ((rc = ensure(ctx, hrg_ctx::W_SEGCNT, sizeof(int32_t) * heavy_cap, &scnt))) return rc;
         b.heavy = (int4 *)heavy;
+        b.seg_cnt = (int32_t *)scnt;
         b.heavy_cap = (int32_t)heavy_cap;
         CK(cudaMemsetAsync(stats, 0, sizeof(uint64_t) * 8, st));
-        CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 4, st));
+        CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 8, st));
         CK(cudaMemsetAsync(bigtot, 0, sizeof(int64_t), st));
         CK(cudaMemsetAsync(deg, 0, sizeof(int32_t) * n, st));
         CK(cudaMemsetAsync(small_cur, 0, sizeof(unsigned long long), st));
@@ -410,6 +377,71 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     J.open = true;
     *n_entries = J.n_entries;
     return HRG_OK;
+}
+
+static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params *prm, int64_t n, double R,
+                        double alpha, const double *r_in, const double *phi_in, double *r_out, double *phi_out,
+                        uint32_t flags, int32_t bands, cudaStream_t st, int64_t *row_off_out, int64_t *n_entries)
+{
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    J = hrg_job();
+    J.ctx = ctx;
+    J.stream = st;
+    J.fp64 = (flags & HRG_FLAG_FP64_ONLY) != 0 || R > 80.0;
+    J.row_off = row_off_out;
+    Plan &p = J.plan;
+    plan_bands(p, n, R, alpha, bands);
+
+    void *band_cnt, *gbuf, *slot, *A, *pms, *pms64 = nullptr, *scanws;
+    int rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_BANDCNT, sizeof(int64_t) * HRG_MAX_BANDS, &band_cnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_GBUF, sizeof(int32_t) * n, &gbuf))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_SLOT, sizeof(int32_t) * n, &slot))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_A, sizeof(uint64_t) * n, &A))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_PMS, sizeof(PMS) * n, &pms))) return rc;
+    if (J.fp64 && (rc = ensure(ctx, hrg_ctx::W_PMS64, sizeof(PMS64) * n, &pms64))) return rc;
+
+    // 1. points and band counts
+    CK(cudaEventRecord(ctx->ev[0], st));
+    CK(cudaMemsetAsync(band_cnt, 0, sizeof(int64_t) * HRG_MAX_BANDS, st));
+    if (sampled) {
+        CK(launch_sample(p, prm->seed, r_out, phi_out, (int64_t *)band_cnt, st));
+        J.r = r_out;
+        J.phi = phi_out;
+    } else {
+        CK(launch_count_bands(p, r_in, phi_in, (int64_t *)band_cnt, st));
+        J.r = r_in;
+        J.phi = phi_in;
+    }
+    CK(cudaEventRecord(ctx->ev[1], st));
+    int64_t *h_cnt = (int64_t *)ctx->pinned;
+    CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int64_t cnt_copy[HRG_MAX_BANDS];
+    memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
+    plan_buckets(p, cnt_copy, &J.p_hub, (prm && prm->hub_candidates > 0) ? (double)prm->hub_candidates : 512.0);
+
+    // 2. counting sort by (band, angular bucket)
+    void *cnt, *start;
+    const size_t scan_bytes = std::max(scan_workspace_bytes(p.G), scan_workspace_bytes(n));
+    if ((rc = ensure(ctx, hrg_ctx::W_CNT, sizeof(int32_t) * p.G, &cnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_START, sizeof(int32_t) * (p.G + 1), &start))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_bytes, &scanws))) return rc;
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * p.G, st));
+    CK(launch_bucket_hist(p, J.r, J.phi, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)cnt, st));
+    CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, p.G, scanws, st));
+    CK(launch_scatter_soa(p, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, J.r, J.phi, (uint64_t *)A,
+                          (PMS *)pms, (PMS64 *)pms64, st));
+    CK(cudaEventRecord(ctx->ev[2], st));
+
+    // 3. degrees, 4. row offsets
+    QueryBufs &b = J.qb;
+    b = QueryBufs{};
+    b.A = (uint64_t *)A;
+    b.pms = (PMS *)pms;
+    b.pms64 = (PMS64 *)pms64;
+    b.start = (int32_t *)start;
+    return count_and_offsets(ctx, J, n, st, row_off_out, n_entries);
 }
 
 static int check_params(hrg_ctx *ctx, const hrg_params *p, double *R)
@@ -464,6 +496,154 @@ extern "C" int hrg_generate_from_points_begin(hrg_ctx *ctx, int64_t n, double R,
         return rc;
     }
     *job = &ctx->job;
+    return HRG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches: many independent graphs through one pass of every stage.  Graph g
+// owns positions, global ids and CSR rows [off_g, off_g + n_g) with off the
+// prefix sum of the n's; its buckets follow those of graph g-1.  The band
+// layout of each graph is planned from the expected band counts of Eq. (1)
+// (n times the radial CDF mass of the band), so planning needs no read-back.
+// ---------------------------------------------------------------------------
+static void expected_band_counts(const Plan &p, int64_t *cnt)
+{
+    // radial CDF of Eq. (1): F(r) = (cosh(alpha r) - 1) / (cosh(alpha R) - 1)
+    double prev = 0.0;
+    for (int k = 0; k < p.B; ++k) {
+        const double hi = (k + 1 < p.B) ? (std::cosh(p.alpha * p.band_lo[k + 1]) - 1.0) / p.big : 1.0;
+        cnt[k] = (int64_t)std::llround((double)p.n * std::max(0.0, hi - prev));
+        prev = hi;
+    }
+}
+
+extern "C" int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_params *items, uint32_t flags,
+                                        void *stream, double *r_out, double *phi_out, int64_t *row_off_out,
+                                        hrg_job **job, int64_t *n_entries)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (!items || !job || !n_entries || !r_out || !phi_out || !row_off_out)
+        return set_err(ctx, HRG_EINVAL, "null argument");
+    if (count < 1 || count > (1 << 24)) return set_err(ctx, HRG_EINVAL, "count must be in [1, 2^24]");
+    if (ctx->job.open) return set_err(ctx, HRG_ESTATE, "a job of this context is still open");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    hrg_job &J = ctx->job;
+    J = hrg_job();
+    J.ctx = ctx;
+    J.stream = st;
+    J.row_off = row_off_out;
+    J.batch = count;
+
+    // plans on the host
+    std::vector<Plan> &plans = ctx->batch_plans;
+    std::vector<int64_t> &noff = ctx->batch_noff, &soff = ctx->batch_soff;
+    plans.resize(count);
+    noff.assign(count + 1, 0);
+    soff.assign(count + 1, 0);
+    int64_t N = 0, G = 0, S = 0;
+    bool fp64 = (flags & HRG_FLAG_FP64_ONLY) != 0;
+    for (int32_t g = 0; g < count; ++g) {
+        double R;
+        int rc = check_params(ctx, &items[g], &R);
+        if (rc) return set_err(ctx, rc, "item %d: %s", g, ctx->err.c_str());
+        fp64 = fp64 || R > 80.0;
+        Plan &p = plans[g];
+        plan_bands(p, items[g].n, R, items[g].alpha, items[g].bands);
+        int64_t cnt[HRG_MAX_BANDS];
+        expected_band_counts(p, cnt);
+        int32_t ph = 0;
+        plan_buckets(p, cnt, &ph, items[g].hub_candidates > 0 ? (double)items[g].hub_candidates : 512.0);
+        noff[g] = N;
+        soff[g] = S;
+        p.id_off = (int32_t)N;
+        p.seed = items[g].seed;
+        for (int k = 0; k <= p.B; ++k) p.base[k] += G;
+        N += p.n;
+        G += p.G;
+        if (p.hub_bands < p.B) S += (int64_t)1 << p.sbits;
+        if (N > 0x7fffffffLL || G > 0x7fffffffLL) return set_err(ctx, HRG_EINVAL, "batch larger than 2^31 points");
+    }
+    noff[count] = N;
+    soff[count] = S;
+    J.fp64 = fp64;
+    J.plan = plans[0];
+    J.plan.n = N;
+    J.batch_G = G;
+
+    // device tables
+    void *d_plans, *d_noff, *d_soff, *graph_of, *gbuf, *slot, *A, *pms, *pms64 = nullptr, *cnt, *start, *scanws;
+    void *hub_cnt, *hub_off, *hub_pos = nullptr;
+    int rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_PLANS, sizeof(Plan) * count, &d_plans))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_NOFF, sizeof(int64_t) * (count + 1), &d_noff))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_SOFF, sizeof(int64_t) * (count + 1), &d_soff))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_GRAPHOF, sizeof(int32_t) * N, &graph_of))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_GBUF, sizeof(int32_t) * N, &gbuf))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_SLOT, sizeof(int32_t) * N, &slot))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_A, sizeof(uint64_t) * N, &A))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_PMS, sizeof(PMS) * N, &pms))) return rc;
+    if (fp64 && (rc = ensure(ctx, hrg_ctx::W_PMS64, sizeof(PMS64) * N, &pms64))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_CNT, sizeof(int32_t) * G, &cnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_START, sizeof(int32_t) * (G + 1), &start))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_HUBCNT, sizeof(int32_t) * (count + 1), &hub_cnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_HUBOFF, sizeof(int32_t) * (count + 1), &hub_off))) return rc;
+    const size_t scan_bytes = std::max(std::max(scan_workspace_bytes(G), scan_workspace_bytes(N)),
+                                       scan_workspace_bytes(count));
+    if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_bytes, &scanws))) return rc;
+    CK(cudaMemcpyAsync(d_plans, plans.data(), sizeof(Plan) * count, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_noff, noff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_soff, soff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
+
+    // 1. points
+    const Plan *P = (const Plan *)d_plans;
+    CK(cudaEventRecord(ctx->ev[0], st));
+    CK(launch_graph_of(P, count, (int32_t *)graph_of, st));
+    CK(launch_sample_batch(P, (int32_t *)graph_of, N, r_out, phi_out, st));
+    J.r = r_out;
+    J.phi = phi_out;
+    CK(cudaEventRecord(ctx->ev[1], st));
+
+    // 2. counting sort by (graph, band, angular bucket); hub query list
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * G, st));
+    CK(launch_bucket_hist_batch(P, (int32_t *)graph_of, N, r_out, phi_out, (int32_t *)gbuf, (int32_t *)slot,
+                                (int32_t *)cnt, st));
+    CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, G, scanws, st));
+    CK(launch_scatter_soa_batch(P, (int32_t *)graph_of, N, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, r_out,
+                                phi_out, (uint64_t *)A, (PMS *)pms, (PMS64 *)pms64, st));
+    CK(launch_hub_list(P, count, (int32_t *)start, (int32_t *)hub_cnt, (int32_t *)hub_off, nullptr, scanws, st,
+                       false));
+    int32_t *hh = (int32_t *)ctx->pinned;
+    CK(cudaMemcpyAsync(hh, (int32_t *)hub_off + count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    J.p_hub = *hh;
+    if (J.p_hub > 0) {
+        if ((rc = ensure(ctx, hrg_ctx::W_HUBPOS, sizeof(int32_t) * J.p_hub, &hub_pos))) return rc;
+        CK(launch_hub_list(P, count, (int32_t *)start, (int32_t *)hub_cnt, (int32_t *)hub_off, (int32_t *)hub_pos,
+                           scanws, st, true));
+    }
+    CK(cudaEventRecord(ctx->ev[2], st));
+
+    // 3. degrees, 4. row offsets
+    QueryBufs &b = J.qb;
+    b = QueryBufs{};
+    b.A = (uint64_t *)A;
+    b.pms = (PMS *)pms;
+    b.pms64 = (PMS64 *)pms64;
+    b.start = (int32_t *)start;
+    b.plans = P;
+    b.graph_of = (int32_t *)graph_of;
+    b.sec_off = (int64_t *)d_soff;
+    b.hub_pos = (int32_t *)hub_pos;
+    b.noff = (int64_t *)d_noff;
+    b.NG = count;
+    b.n_sectors = S;
+    rc = count_and_offsets(ctx, J, N, st, row_off_out, n_entries);
+    if (rc) {
+        J.open = false;
+        return rc;
+    }
+    *job = &J;
     return HRG_OK;
 }
 
@@ -528,11 +708,21 @@ extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
     out->mu = job->plan.mu;
     for (int k = 0; k < 8; ++k) out->stage_ms[k] = job->stage_ms[k];
     // kernels launched: points (1), bucket histogram (1), bucket scan,
-    // scatter (1), structure-of-arrays (1), count (1-2), row-offset scan,
-    // write (1-2), row sorts (mid 1, big 5)
+    // structure-of-arrays scatter (1), count (hub 3, rim 1), row-offset scan,
+    // write (hub 3, rim 1), row sorts (warp 1, CTA 1, big 7)
     const int64_t n = job->plan.n;
-    int L = 1 + 1 + scan_launches(job->plan.G) + 1 + 1 + query_launches(job->plan, job->p_hub, false) +
-            scan_launches(n);
+    int L;
+    if (job->batch) {
+        // graph map, points, bucket histogram, bucket scan, structure-of-arrays
+        // scatter, hub count + scan (+ fill), count, row-offset scan
+        L = 1 + 1 + 1 + scan_launches(job->batch_G) + 1 + 1 + scan_launches(job->batch) +
+            (job->p_hub > 0 ? 1 : 0) + (job->p_hub > 0 ? 3 : 0) + (job->qb.n_sectors > 0 ? 1 : 0) + scan_launches(n);
+        if (job->finished) L += (job->p_hub > 0 ? 3 : 0) + (job->qb.n_sectors > 0 ? 1 : 0) + sort_launches(job->lists);
+        out->launches = L;
+        out->buckets = job->batch_G;
+        return HRG_OK;
+    }
+    L = 1 + 1 + scan_launches(job->plan.G) + 1 + query_launches(job->plan, job->p_hub, false) + scan_launches(n);
     if (job->finished) L += query_launches(job->plan, job->p_hub, true) + sort_launches(job->lists);
     out->launches = L;
     return HRG_OK;

@@ -22,6 +22,7 @@ struct Plan {
     int64_t n;
     double R, coshR, alpha;
     double big;          // cosh(alpha R) - 1, the scale of Eq. (1)'s inverse CDF
+    double inv_alpha;    // 1 / alpha
     double half_R;       // R / 2
     double inv_width;    // B / R
     int B;               // number of radial bands
@@ -35,6 +36,12 @@ struct Plan {
     float rhs32;         // 1 + e^{-2R} rounded to float
     float mu;            // half-width of the FP32 filter's undecided band (relative)
     double rhs64;        // 1 + e^{-2R}
+    // A batch of graphs lays its graphs out one after another: graph g owns
+    // positions and global ids [id_off, id_off + n) and buckets from base[0].
+    // The CSR stores local ids (global id - id_off).  0 for a single graph.
+    int32_t id_off;
+    int32_t pad_;
+    uint64_t seed;       // Philox key of the graph (batches)
 };
 
 // ---------------------------------------------------------------------------
@@ -60,6 +67,17 @@ __device__ __forceinline__ U4 philox_block(uint64_t ctr, uint64_t seed)
         kb += BUMP_B;
     }
     return s;
+}
+
+// Radius of Eq. (1)'s inverse CDF, r = acosh(x) / alpha with x = 1 + u_r
+// (cosh(alpha R) - 1).  For x >= 2^24, acosh(x) = log(2x) - 1/(4x^2) - ...
+// and the dropped terms are below 2^-50 against log(2x) > 17: log alone is
+// exact to well under an ulp there (and skips acosh's square root).
+__device__ __forceinline__ double radius_of(double u_r, double big, double inv_alpha)
+{
+    const double x = __dadd_rn(1.0, __dmul_rn(u_r, big));
+    const double a = x >= 0x1p24 ? log(x + x) : acosh(x);
+    return a * inv_alpha;
 }
 
 // the uniform on [0,1) made of the top 53 bits of a 64-bit word

@@ -12,16 +12,32 @@ namespace hrg {
 cudaError_t launch_sample(const Plan &p, uint64_t seed, double *r, double *phi, int64_t *band_cnt, cudaStream_t s);
 // Per-band point counts of an injected point set.
 cudaError_t launch_count_bands(const Plan &p, const double *r, const double *phi, int64_t *band_cnt, cudaStream_t s);
-// Angular-bucket id of every point (gbuf, id order) and bucket occupancy.
-cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi, int32_t *gbuf, int32_t *cnt,
+// Angular-bucket id of every point (gbuf, id order), bucket occupancy (cnt)
+// and the point's rank inside its bucket (slot; order inside a bucket is
+// unspecified).
+cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi, int32_t *gbuf, int32_t *slot,
+                               int32_t *cnt, cudaStream_t s);
+// Structure-of-arrays in bucket order (point i at start[gbuf[i]] + slot[i]):
+// fixed-point angle, FP32 scaled exps + id; optionally the FP64 data of the
+// plain double-precision path.
+cudaError_t launch_scatter_soa(const Plan &p, const int32_t *gbuf, const int32_t *slot, const int32_t *start,
+                               const double *r, const double *phi, uint64_t *A, PMS *pms, PMS64 *pms64,
                                cudaStream_t s);
-// perm[start[g] ..] = ids of bucket g (order inside a bucket unspecified).
-cudaError_t launch_bucket_scatter(const Plan &p, const int32_t *gbuf, const int32_t *start, int32_t *cnt,
-                                  int32_t *perm, cudaStream_t s);
-// Structure-of-arrays in bucket order: fixed-point angle, FP32 scaled exps
-// + id; optionally the FP64 data of the plain double-precision path.
-cudaError_t launch_build_soa(const Plan &p, const int32_t *perm, const double *r, const double *phi, uint64_t *A,
-                             PMS *pms, PMS64 *pms64, cudaStream_t s);
+
+// Batches: plans[NG] in device memory, graph g owning positions and global
+// ids [plans[g].id_off, plans[g].id_off + plans[g].n).
+cudaError_t launch_graph_of(const Plan *plans, int NG, int32_t *graph_of, cudaStream_t s);
+cudaError_t launch_sample_batch(const Plan *plans, const int32_t *graph_of, int64_t N, double *r, double *phi,
+                                cudaStream_t s);
+cudaError_t launch_bucket_hist_batch(const Plan *plans, const int32_t *graph_of, int64_t N, const double *r,
+                                     const double *phi, int32_t *gbuf, int32_t *slot, int32_t *cnt, cudaStream_t s);
+cudaError_t launch_scatter_soa_batch(const Plan *plans, const int32_t *graph_of, int64_t N, const int32_t *gbuf,
+                                     const int32_t *slot, const int32_t *start, const double *r, const double *phi,
+                                     uint64_t *A, PMS *pms, PMS64 *pms64, cudaStream_t s);
+// hub queries of every graph: fill=false counts them (hub_cnt[NG]) and scans
+// into hub_off[NG+1]; fill=true writes their positions into hub_pos
+cudaError_t launch_hub_list(const Plan *plans, int NG, const int32_t *start, int32_t *hub_cnt, int32_t *hub_off,
+                            int32_t *hub_pos, void *ws, cudaStream_t s, bool fill);
 
 // Exclusive prefix sums with the total stored at out[N].
 size_t scan_workspace_bytes(int64_t N);
@@ -44,16 +60,29 @@ struct QueryBufs {
     int32_t *deg;             // [n] id order
     unsigned long long *stats;  // [8] counters: candidates, rechecks, edges, ..., [7] error flag
     int32_t *rows[3];         // ids of rows to sort: (kRegRow, kWarpRow], (kWarpRow, kSmemRow], > kSmemRow
-    int32_t *list_cnt;        // [4] lengths of the three lists, [3] heavy segments
+    int32_t *list_cnt;        // [8] lengths: [0..2] the three sort lists, [3] heavy segments,
+                              //     [4] kept rim rows, [5] rim rows to traverse again
+    int32_t *kept;            // [n] positions of rim queries whose row the count pass kept
+    int32_t *relist;          // [n] positions of rim queries the write pass traverses again
     int64_t *big_total;       // [1] sum of degrees of the longest rows
     int4 *heavy;              // [heavy_cap] (query position, 2*band+part, begin, end) of long hub ranges
     int32_t heavy_cap;
-    int32_t *cursor;          // [p_hub] write cursor of each hub row
+    int32_t *cursor;          // [p_hub] write cursor of each hub row's heavy segments
+    int32_t *warp_cnt;        // [p_hub] entries a hub query's own warp found (count pass)
+    int32_t *seg_cnt;         // [heavy_cap] entries found in each heavy segment (count pass)
     int32_t *col_out;         // CSR neighbour ids being written (write pass only)
     int32_t *small;           // [small_cap] sorted rim rows of up to kRegRow entries kept by the count pass
     int32_t *small_off;       // [n] by position: start of the kept row in small, -1 if not kept
     unsigned long long *small_cursor;  // [1] bump allocator over small
     int64_t small_cap;
+    // batches of graphs (null / 0 for a single graph)
+    const Plan *plans;        // [NG] the graphs' plans in device memory
+    const int32_t *graph_of;  // [N] graph of every position (= of every global id)
+    const int64_t *sec_off;   // [NG+1] first global rim sector of each graph
+    const int32_t *hub_pos;   // [hub queries] position of each hub query
+    const int64_t *noff;      // [NG+1] first global id of each graph
+    int32_t NG;
+    int64_t n_sectors;        // rim sectors over all graphs
 };
 
 constexpr int kHeavy = 4096;      // hub ranges longer than this are split into chunks for whole CTAs
@@ -64,9 +93,11 @@ cudaError_t launch_count_hub(const Plan &p, const QueryBufs &b, bool fp64_only, 
 // Degrees of rim-band vertices (one CTA per angular sector, one thread per vertex).
 cudaError_t launch_count_rim(const Plan &p, const QueryBufs &b, bool fp64_only, cudaStream_t s);
 // Same traversals, writing neighbour ids into col_idx[row_off[id] ..]; hub
-// rows are written through cursor[] in no particular order (sorted later).
+// rows are written in no particular order (sorted later): the query's warp
+// first, then its heavy segments, each at an offset reserved with one atomic.
 cudaError_t launch_write_hub(const Plan &p, const QueryBufs &b, bool fp64_only, int32_t p_hub,
                              const int64_t *row_off, int32_t *col_idx, cudaStream_t s);
+// Rim rows: kept rows are sorted and copied, the others traversed again.
 cudaError_t launch_write_rim(const Plan &p, const QueryBufs &b, bool fp64_only, const int64_t *row_off,
                              int32_t *col_idx, cudaStream_t s);
 int query_launches(const Plan &p, int32_t p_hub, bool write);

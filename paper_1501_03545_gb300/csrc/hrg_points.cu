@@ -46,7 +46,7 @@ __global__ void k_sample(Plan p, uint64_t seed, double *__restrict__ r_out, doub
         const double u_phi = unit53(w.x, w.y);
         const double u_r = unit53(w.z, w.w);
         const double phi = __dmul_rn(u_phi, kTwoPi);
-        const double r = __ddiv_rn(acosh(__dadd_rn(1.0, __dmul_rn(u_r, p.big))), p.alpha);
+        const double r = radius_of(u_r, p.big, p.inv_alpha);
         phi_out[i] = phi;
         r_out[i] = r;
         atomicAdd(&sh[band_of(p, r)], 1);
@@ -65,41 +65,112 @@ __global__ void k_count_bands(Plan p, const double *__restrict__ r, int64_t *__r
     band_hist_flush(p, sh, band_cnt);
 }
 
+// Bucket of every point (gbuf, id order), bucket occupancy, and the point's
+// rank inside its bucket (slot: the count it found there).
 __global__ void k_bucket_hist(Plan p, const double *__restrict__ r, const double *__restrict__ phi,
-                              int32_t *__restrict__ gbuf, int32_t *__restrict__ cnt)
+                              int32_t *__restrict__ gbuf, int32_t *__restrict__ slot, int32_t *__restrict__ cnt)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
         const int band = band_of(p, r[i]);
         const int64_t g = bucket_of(p, band, angle_key(phi[i]));
         gbuf[i] = (int32_t)g;
-        atomicAdd(&cnt[g], 1);
+        slot[i] = atomicAdd(&cnt[g], 1);
     }
 }
 
-__global__ void k_bucket_scatter(int64_t n, const int32_t *__restrict__ gbuf, const int32_t *__restrict__ start,
-                                 int32_t *__restrict__ cnt, int32_t *__restrict__ perm)
+// Structure of arrays in (band, bucket) order, written from id order: point i
+// goes to position start[gbuf[i]] + slot[i].
+__device__ __forceinline__ void place_point(const Plan &p, int64_t i, const int32_t *__restrict__ gbuf,
+                                            const int32_t *__restrict__ slot, const int32_t *__restrict__ start,
+                                            const double *__restrict__ r, const double *__restrict__ phi,
+                                            uint64_t *__restrict__ A, PMS *__restrict__ pms,
+                                            PMS64 *__restrict__ pms64)
+{
+    const int64_t k = (int64_t)__ldg(start + gbuf[i]) + slot[i];
+    const double rr = r[i], ph = phi[i];
+    A[k] = angle_key(ph);
+    pms[k] = scaled_exps(p, rr, (int32_t)i);
+    if (pms64) pms64[k] = scaled_exps64(p, rr, ph);
+}
+
+__global__ void k_scatter_soa(Plan p, const int32_t *__restrict__ gbuf, const int32_t *__restrict__ slot,
+                              const int32_t *__restrict__ start, const double *__restrict__ r,
+                              const double *__restrict__ phi, uint64_t *__restrict__ A, PMS *__restrict__ pms,
+                              PMS64 *__restrict__ pms64)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int32_t g = gbuf[i];
-        const int32_t slot = atomicSub(&cnt[g], 1) - 1;
-        perm[start[g] + slot] = (int32_t)i;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride)
+        place_point(p, i, gbuf, slot, start, r, phi, A, pms, pms64);
+}
+
+// ---------------------------------------------------------------------------
+// Batches of graphs.  Graph g owns positions and global ids [off_g, off_g +
+// n_g); graph_of[] maps either back to g.  Each kernel is the single-graph
+// kernel above with the plan looked up per point.
+// ---------------------------------------------------------------------------
+__global__ void k_graph_of(const Plan *__restrict__ plans, int32_t *__restrict__ graph_of)
+{
+    const int g = blockIdx.x;
+    const int64_t off = plans[g].id_off, n = plans[g].n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) graph_of[off + i] = g;
+}
+
+__global__ void k_sample_batch(const Plan *__restrict__ plans, const int32_t *__restrict__ graph_of, int64_t N,
+                               double *__restrict__ r_out, double *__restrict__ phi_out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const Plan &p = plans[__ldg(graph_of + i)];
+        const U4 w = philox_block((uint64_t)(i - p.id_off), p.seed);
+        const double u_phi = unit53(w.x, w.y);
+        const double u_r = unit53(w.z, w.w);
+        phi_out[i] = __dmul_rn(u_phi, kTwoPi);
+        r_out[i] = radius_of(u_r, p.big, p.inv_alpha);
     }
 }
 
-__global__ void k_build_soa(Plan p, const int32_t *__restrict__ perm, const double *__restrict__ r,
-                            const double *__restrict__ phi, uint64_t *__restrict__ A, PMS *__restrict__ pms,
-                            PMS64 *__restrict__ pms64)
+__global__ void k_bucket_hist_batch(const Plan *__restrict__ plans, const int32_t *__restrict__ graph_of, int64_t N,
+                                    const double *__restrict__ r, const double *__restrict__ phi,
+                                    int32_t *__restrict__ gbuf, int32_t *__restrict__ slot, int32_t *__restrict__ cnt)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.n; k += stride) {
-        const int32_t id = perm[k];
-        const double rr = r[id], ph = phi[id];
-        A[k] = angle_key(ph);
-        pms[k] = scaled_exps(p, rr, id);
-        if (pms64) pms64[k] = scaled_exps64(p, rr, ph);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const Plan &p = plans[__ldg(graph_of + i)];
+        const int band = band_of(p, r[i]);
+        const int64_t g = bucket_of(p, band, angle_key(phi[i]));
+        gbuf[i] = (int32_t)g;
+        slot[i] = atomicAdd(&cnt[g], 1);
     }
+}
+
+__global__ void k_scatter_soa_batch(const Plan *__restrict__ plans, const int32_t *__restrict__ graph_of, int64_t N,
+                                    const int32_t *__restrict__ gbuf, const int32_t *__restrict__ slot,
+                                    const int32_t *__restrict__ start, const double *__restrict__ r,
+                                    const double *__restrict__ phi, uint64_t *__restrict__ A, PMS *__restrict__ pms,
+                                    PMS64 *__restrict__ pms64)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+        place_point(plans[__ldg(graph_of + i)], i, gbuf, slot, start, r, phi, A, pms, pms64);
+}
+
+// hub queries of graph g: its positions before its first rim-band bucket
+__global__ void k_hub_count(const Plan *__restrict__ plans, int NG, const int32_t *__restrict__ start,
+                            int32_t *__restrict__ hub_cnt)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= NG) return;
+    const Plan &p = plans[g];
+    hub_cnt[g] = __ldg(start + p.base[p.hub_bands]) - p.id_off;
+}
+
+__global__ void k_hub_fill(const Plan *__restrict__ plans, const int32_t *__restrict__ hub_off,
+                           int32_t *__restrict__ hub_pos)
+{
+    const int g = blockIdx.x;
+    const int32_t o = hub_off[g], c = hub_off[g + 1] - o, first = plans[g].id_off;
+    for (int32_t t = threadIdx.x; t < c; t += blockDim.x) hub_pos[o + t] = first + t;
 }
 
 // ---------------------------------------------------------------------------
@@ -246,24 +317,57 @@ cudaError_t launch_count_bands(const Plan &p, const double *r, const double *, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi, int32_t *gbuf, int32_t *cnt,
-                               cudaStream_t s)
+cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi, int32_t *gbuf, int32_t *slot,
+                               int32_t *cnt, cudaStream_t s)
 {
-    k_bucket_hist<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, r, phi, gbuf, cnt);
+    k_bucket_hist<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, r, phi, gbuf, slot, cnt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bucket_scatter(const Plan &p, const int32_t *gbuf, const int32_t *start, int32_t *cnt,
-                                  int32_t *perm, cudaStream_t s)
+cudaError_t launch_scatter_soa(const Plan &p, const int32_t *gbuf, const int32_t *slot, const int32_t *start,
+                               const double *r, const double *phi, uint64_t *A, PMS *pms, PMS64 *pms64, cudaStream_t s)
 {
-    k_bucket_scatter<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p.n, gbuf, start, cnt, perm);
+    k_scatter_soa<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, gbuf, slot, start, r, phi, A, pms, pms64);
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_soa(const Plan &p, const int32_t *perm, const double *r, const double *phi, uint64_t *A,
-                             PMS *pms, PMS64 *pms64, cudaStream_t s)
+cudaError_t launch_graph_of(const Plan *plans, int NG, int32_t *graph_of, cudaStream_t s)
 {
-    k_build_soa<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, perm, r, phi, A, pms, pms64);
+    k_graph_of<<<NG, 256, 0, s>>>(plans, graph_of);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_batch(const Plan *plans, const int32_t *graph_of, int64_t N, double *r, double *phi,
+                                cudaStream_t s)
+{
+    k_sample_batch<<<grid_for(N, kThreads, 4), kThreads, 0, s>>>(plans, graph_of, N, r, phi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_hist_batch(const Plan *plans, const int32_t *graph_of, int64_t N, const double *r,
+                                     const double *phi, int32_t *gbuf, int32_t *slot, int32_t *cnt, cudaStream_t s)
+{
+    k_bucket_hist_batch<<<grid_for(N, kThreads, 4), kThreads, 0, s>>>(plans, graph_of, N, r, phi, gbuf, slot, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_soa_batch(const Plan *plans, const int32_t *graph_of, int64_t N, const int32_t *gbuf,
+                                     const int32_t *slot, const int32_t *start, const double *r, const double *phi,
+                                     uint64_t *A, PMS *pms, PMS64 *pms64, cudaStream_t s)
+{
+    k_scatter_soa_batch<<<grid_for(N, kThreads, 4), kThreads, 0, s>>>(plans, graph_of, N, gbuf, slot, start, r, phi,
+                                                                       A, pms, pms64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hub_list(const Plan *plans, int NG, const int32_t *start, int32_t *hub_cnt, int32_t *hub_off,
+                            int32_t *hub_pos, void *ws, cudaStream_t s, bool fill)
+{
+    if (!fill) {
+        k_hub_count<<<(NG + 255) / 256, 256, 0, s>>>(plans, NG, start, hub_cnt);
+        return scan_i32_to_i32(hub_cnt, hub_off, NG, ws, s);
+    }
+    k_hub_fill<<<NG, 256, 0, s>>>(plans, hub_off, hub_pos);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ namespace {
 
 enum { ST_CAND = 0, ST_RECHECK = 1, ST_EDGES = 2, ST_ERR = 7 };
 
+
 // Candidate positions of a query in band j: up to two ranges [s0,e0) [s1,e1)
 struct Ranges { int32_t s0, e0, s1, e1; uint64_t W; };
 
@@ -46,12 +47,13 @@ __device__ __forceinline__ Ranges band_ranges(const Plan &p, const int32_t *__re
     if (W != kFullCircle && g != 0) {
         const uint64_t lo = Aq - W, hi = Aq + W;
         const int64_t bl = (int64_t)(lo >> (64 - g)), bh = (int64_t)(hi >> (64 - g));
-        i0 = bl;
         if (lo <= hi) {
+            i0 = bl;
             i1 = bh + 1;
-        } else {  // the window wraps through angle 0
+        } else if (bh < bl) {  // the window wraps through angle 0
+            i0 = bl;
             i3 = bh + 1;
-        }
+        }  // else it wraps and leaves a gap inside one bucket: the whole band, once
     }
     rg.s0 = __ldg(start + b0 + i0);
     rg.e0 = __ldg(start + b0 + i1);
@@ -133,48 +135,82 @@ __device__ __forceinline__ void bitonic_regs(int32_t (&v)[kRegRow])
             }
 }
 
+// list[...] += v for the lanes with e: one atomic per warp
+__device__ __forceinline__ void warp_append(int32_t *list, int32_t *count, bool e, int32_t v, int lane)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, e);
+    if (m == 0) return;
+    int32_t base = 0;
+    if (lane == 0) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (e) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
 // ---------------------------------------------------------------------------
 // One query, one thread (rim bands).  Rows of up to kRegRow entries are kept
 // sorted in registers.  The count pass stores such a row in the row buffer
 // (b.small) and records where (b.small_off[position]); the write pass then
-// copies it instead of traversing the query again.  Longer rows, and rows
-// that did not fit in the buffer, are traversed again by the write pass.
+// copies it instead of traversing the query again (write_stored).  Longer
+// rows, and rows that did not fit in the buffer, are traversed again by the
+// write pass.
 // ---------------------------------------------------------------------------
+// write pass, row kept by the count pass: sort it in registers and store it;
+// false if the row was not kept
+__device__ __forceinline__ bool write_stored(const Plan &p, const QueryBufs &b, int32_t qp,
+                                             const int64_t *__restrict__ row_off, int32_t *__restrict__ col_idx)
+{
+    const int32_t stored = b.small_off[qp];
+    if (stored < 0) return false;
+    const int32_t id = b.pms[qp].id;
+    const int64_t base = row_off[id];
+    const int32_t deg = (int32_t)(row_off[id + 1] - base);
+    int32_t v[kRegRow];
+#pragma unroll
+    for (int k = 0; k < kRegRow; ++k) v[k] = k < deg ? b.small[stored + k] : 0x7fffffff;
+    if (deg > 16) bitonic_regs<32>(v);
+    else if (deg > 8) bitonic_regs<16>(v);
+    else if (deg > 4) bitonic_regs<8>(v);
+    else if (deg > 1) bitonic_regs<4>(v);
+#pragma unroll
+    for (int k = 0; k < kRegRow; ++k)
+        if (k < deg) col_idx[base + k] = v[k] - p.id_off;
+    return true;
+}
+
+// The traversal.  Count pass: every query of the sector; write pass: only
+// queries whose row was not kept (no warp-collective operations there, so
+// the write pass may call it for any subset of lanes).
 template <bool F64, bool WRITE>
 __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, int32_t qp, bool active,
                                              const int64_t *__restrict__ row_off, int32_t *__restrict__ col_idx,
                                              unsigned &n_cand, unsigned &n_re, unsigned &n_edge)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
     PMS q{};
     int64_t base = 0;
     int32_t deg = 0;
-    int32_t stored = -1;
     if (active) {
         q = b.pms[qp];
         if (WRITE) {
             base = row_off[q.id];
             deg = (int32_t)(row_off[q.id + 1] - base);
-            stored = b.small_off[qp];
         }
-    }
-    if (WRITE && active && stored >= 0) {
-        // the count pass kept this row (unsorted): sort it in registers, store it
-        int32_t v[kRegRow];
-#pragma unroll
-        for (int k = 0; k < kRegRow; ++k) v[k] = k < deg ? b.small[stored + k] : 0x7fffffff;
-        if (deg > 16) bitonic_regs<32>(v);
-        else if (deg > 8) bitonic_regs<16>(v);
-        else if (deg > 4) bitonic_regs<8>(v);
-        else if (deg > 1) bitonic_regs<4>(v);
-#pragma unroll
-        for (int k = 0; k < kRegRow; ++k)
-            if (k < deg) col_idx[base + k] = v[k];
-        return;
     }
     int32_t buf[kRegRow];
     int32_t cnt = 0;
+    auto edge = [&](int32_t id) {
+        if (WRITE) {
+            if (cnt < kRegRow) {  // insertion into the sorted list (rows not kept)
+                int32_t k = cnt;
+                while (k > 0 && buf[k - 1] > id) { buf[k] = buf[k - 1]; --k; }
+                buf[k] = id;
+            }
+            if (deg > kRegRow && cnt < deg) col_idx[base + cnt] = id - p.id_off;
+        } else if (cnt < kRegRow) {
+            buf[cnt] = id;  // count pass: kept unsorted
+        }
+        ++cnt;
+    };
     if (active) {
         const uint64_t Aq = b.A[qp];
         PMS64 q64{};
@@ -188,19 +224,7 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
                     const uint64_t Ac = __ldg(b.A + c);
                     if (rg.W != kFullCircle && !within(Aq, Ac, rg.W)) continue;
                     const PMS cc = b.pms[c];
-                    if (decide_loaded<F64>(p, b, q, q64, Aq, Ac, cc, c, kFullCircle, n_cand, n_re)) {
-                        if (WRITE) {
-                            if (cnt < kRegRow) {  // insertion into the sorted list (rows not kept)
-                                int32_t k = cnt;
-                                while (k > 0 && buf[k - 1] > cc.id) { buf[k] = buf[k - 1]; --k; }
-                                buf[k] = cc.id;
-                            }
-                            if (deg > kRegRow && cnt < deg) col_idx[base + cnt] = cc.id;
-                        } else if (cnt < kRegRow) {
-                            buf[cnt] = cc.id;  // count pass: kept unsorted
-                        }
-                        ++cnt;
-                    }
+                    if (decide_loaded<F64>(p, b, q, q64, Aq, Ac, cc, c, kFullCircle, n_cand, n_re)) edge(cc.id);
                 }
             }
         }
@@ -209,7 +233,7 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
         if (active) {
             if (cnt != deg) atomicOr((unsigned long long *)&b.stats[ST_ERR], 1ull);
             if (deg <= kRegRow)
-                for (int32_t k = 0; k < cnt && k < deg; ++k) col_idx[base + k] = buf[k];
+                for (int32_t k = 0; k < cnt && k < deg; ++k) col_idx[base + k] = buf[k] - p.id_off;
         }
     } else {
         // keep rows of up to kRegRow entries: warp-aggregated reservation in b.small
@@ -225,10 +249,9 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
         long long wbase = 0;
         if (lane == 31 && tot > 0) wbase = atomicAdd((unsigned long long *)b.small_cursor, (unsigned long long)tot);
         wbase = __shfl_sync(0xffffffffu, wbase, 31);
-        (void)lt;
+        int32_t off = -1;
         if (active) {
             const long long pos = wbase + incl - want;
-            int32_t off = -1;
             if (keep && pos + cnt <= b.small_cap) {
                 for (int32_t k = 0; k < cnt; ++k) b.small[pos + k] = buf[k];
                 off = (int32_t)pos;
@@ -237,6 +260,9 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
             b.deg[q.id] = cnt;
             classify_row(b, q.id, cnt);
         }
+        // the write pass's work lists: kept rows, and rows to traverse again
+        warp_append(b.kept, &b.list_cnt[4], active && off >= 0, qp, lane);
+        warp_append(b.relist, &b.list_cnt[5], active && off < 0 && cnt > 0, qp, lane);
     }
     if (active) n_edge += cnt;
 }
@@ -244,13 +270,11 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
 // One CTA per angular sector: the queries of all rim bands whose angle lies
 // in the sector.  Sector s of band j is the bucket range
 // [s << (g_j - sbits), (s + 1) << (g_j - sbits)) (every band has g_j >= sbits).
-template <bool F64, bool WRITE>
-__global__ void __launch_bounds__(256) k_rim_sector(Plan p, QueryBufs b, const int64_t *__restrict__ row_off,
-                                                    int32_t *__restrict__ col_idx)
+template <bool F64>
+__device__ __forceinline__ void rim_sector(const Plan &p, const QueryBufs &b, int64_t sector)
 {
     __shared__ int32_t s_beg[HRG_MAX_BANDS];
     __shared__ int32_t s_pre[HRG_MAX_BANDS + 1];
-    const int64_t sector = blockIdx.x;
     if (threadIdx.x < HRG_MAX_BANDS) {
         const int j = threadIdx.x;
         int32_t s = 0, e = 0;
@@ -281,9 +305,64 @@ __global__ void __launch_bounds__(256) k_rim_sector(Plan p, QueryBufs b, const i
             while (t >= s_pre[j + 1]) ++j;  // t only grows, so j only moves forward
             qp = s_beg[j] + (t - s_pre[j]);
         }
-        thread_query<F64, WRITE>(p, b, qp, active, row_off, col_idx, n_cand, n_re, n_edge);
+        thread_query<F64, false>(p, b, qp, active, nullptr, nullptr, n_cand, n_re, n_edge);
     }
-    if (!WRITE) add_stats(b.stats, n_cand, n_re, n_edge);
+    add_stats(b.stats, n_cand, n_re, n_edge);
+}
+
+// Write pass of the rim rows.  Kept rows: sort in registers and store.
+template <bool BATCH>
+__global__ void __launch_bounds__(256) k_rim_copy(Plan p, QueryBufs b, const int64_t *__restrict__ row_off,
+                                                  int32_t *__restrict__ col_idx)
+{
+    const int32_t nk = *((volatile int32_t *)&b.list_cnt[4]);
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nk; k += gridDim.x * blockDim.x) {
+        const int32_t qp = b.kept[k];
+        if (BATCH) write_stored(b.plans[__ldg(b.graph_of + qp)], b, qp, row_off, col_idx);
+        else write_stored(p, b, qp, row_off, col_idx);
+    }
+}
+
+// Rows the count pass did not keep (longer than kRegRow, or no room): the
+// traversal again, one thread per row, all such rows side by side.
+template <bool F64, bool BATCH>
+__global__ void __launch_bounds__(256) k_rim_relist(Plan p, QueryBufs b, const int64_t *__restrict__ row_off,
+                                                    int32_t *__restrict__ col_idx)
+{
+    const int32_t nr = *((volatile int32_t *)&b.list_cnt[5]);
+    unsigned n_cand = 0, n_re = 0, n_edge = 0;
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
+        const int32_t qp = b.relist[k];
+        if (BATCH)
+            thread_query<F64, true>(b.plans[__ldg(b.graph_of + qp)], b, qp, true, row_off, col_idx, n_cand, n_re,
+                                    n_edge);
+        else
+            thread_query<F64, true>(p, b, qp, true, row_off, col_idx, n_cand, n_re, n_edge);
+    }
+}
+
+// the graph of global item k of a batch: the last g with off[g] <= k
+__device__ __forceinline__ int graph_search(const int64_t *__restrict__ off, int NG, int64_t k)
+{
+    int lo = 0, hi = NG;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= k) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Count pass.  One graph: block x is sector x.  A batch: block x is global
+// sector x; the sector table gives its graph.
+template <bool F64, bool BATCH>
+__global__ void __launch_bounds__(256) k_rim_sector(Plan p, QueryBufs b)
+{
+    if (BATCH) {
+        const int g = graph_search(b.sec_off, b.NG, blockIdx.x);
+        rim_sector<F64>(b.plans[g], b, (int64_t)blockIdx.x - __ldg(b.sec_off + g));
+    } else {
+        rim_sector<F64>(p, b, blockIdx.x);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -305,28 +384,26 @@ __device__ __forceinline__ Ranges shfl_ranges(const Ranges &r, int src)
     return o;
 }
 
-// warp-aggregated write of this lane's edge (if any) into a hub row
-__device__ __forceinline__ void warp_emit(const QueryBufs &b, int32_t qp, int64_t base, int32_t deg, bool e,
-                                          int32_t id, unsigned lt, int lane)
+// write of this lane's edge (if any) at the warp's running offset pos of a
+// hub row: no atomics, the warp owns [base, base + its count)
+__device__ __forceinline__ void warp_put(int32_t *__restrict__ out, int64_t base, int32_t lim, int32_t &pos, bool e,
+                                         int32_t id, unsigned lt)
 {
     const unsigned m = __ballot_sync(0xffffffffu, e);
-    if (m == 0) return;
-    int32_t slot = 0;
-    if (lane == 0) slot = atomicAdd(&b.cursor[qp], __popc(m));
-    slot = __shfl_sync(0xffffffffu, slot, 0);
     if (e) {
-        const int32_t pos = slot + __popc(m & lt);
-        if (pos < deg) b.col_out[base + pos] = id;
+        const int32_t k = pos + __popc(m & lt);
+        if (k < lim) out[base + k] = id;
     }
+    pos += __popc(m);
 }
 
+// Hub query number qi at position qp (the same for a single graph; the hub
+// list of a batch maps one to the other).
 template <bool F64, bool WRITE>
-__global__ void __launch_bounds__(256) k_hub_warp(Plan p, QueryBufs b, int32_t p_hub,
-                                                  const int64_t *__restrict__ row_off)
+__device__ __forceinline__ void hub_query(const Plan &p, const QueryBufs &b, int32_t qi, int32_t qp,
+                                          const int64_t *__restrict__ row_off)
 {
-    const int32_t qp = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (qp >= p_hub) return;  // uniform per warp
     const PMS q = b.pms[qp];
     const uint64_t Aq = b.A[qp];
     PMS64 q64{};
@@ -343,6 +420,8 @@ __global__ void __launch_bounds__(256) k_hub_warp(Plan p, QueryBufs b, int32_t p
     const unsigned lt = (1u << lane) - 1u;
     unsigned n_cand = 0, n_re = 0;
     int32_t mine = 0;
+    int32_t pos = 0;                               // write pass: entries this warp has written
+    const int32_t lim = WRITE ? b.warp_cnt[qi] : 0;  // ... and must write
     for (int j = 0; j < p.B; ++j) {
         const Ranges rg = shfl_ranges(j < 32 ? rA : rB, j & 31);
         for (int part = 0; part < 2; ++part) {
@@ -353,7 +432,7 @@ __global__ void __launch_bounds__(256) k_hub_warp(Plan p, QueryBufs b, int32_t p
                     for (int32_t k = lane; k < nch; k += 32) {
                         const int32_t idx = atomicAdd(&b.list_cnt[3], 1);
                         if (idx < b.heavy_cap)
-                            b.heavy[idx] = make_int4(qp, 2 * j + part, s + k * kHeavy, min(e, s + (k + 1) * kHeavy));
+                            b.heavy[idx] = make_int4(qi, 2 * j + part, s + k * kHeavy, min(e, s + (k + 1) * kHeavy));
                     }
                 }
                 continue;
@@ -368,8 +447,8 @@ __global__ void __launch_bounds__(256) k_hub_warp(Plan p, QueryBufs b, int32_t p
                 const bool ea = va && decide_loaded<F64>(p, b, q, q64, Aq, Aa, pa, ca, rg.W, n_cand, n_re);
                 const bool eb = vb && decide_loaded<F64>(p, b, q, q64, Aq, Ab, pb, cb, rg.W, n_cand, n_re);
                 if (WRITE) {
-                    warp_emit(b, qp, base, deg, ea, pa.id, lt, lane);
-                    warp_emit(b, qp, base, deg, eb, pb.id, lt, lane);
+                    warp_put(b.col_out, base, lim, pos, ea, pa.id - p.id_off, lt);
+                    warp_put(b.col_out, base, lim, pos, eb, pb.id - p.id_off, lt);
                 } else {
                     mine += (int)ea + (int)eb;
                 }
@@ -380,70 +459,134 @@ __global__ void __launch_bounds__(256) k_hub_warp(Plan p, QueryBufs b, int32_t p
         int32_t d = mine;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        if (lane == 0 && d) atomicAdd(&b.deg[q.id], d);
+        if (lane == 0) {
+            b.warp_cnt[qi] = d;
+            if (d) atomicAdd(&b.deg[q.id], d);
+        }
         add_stats(b.stats, n_cand, n_re, lane == 0 ? (unsigned)d : 0u);
+    } else if (lane == 0 && (pos != lim || lim > deg)) {
+        atomicOr((unsigned long long *)&b.stats[ST_ERR], 1ull);
+    }
+    (void)deg;
+}
+
+template <bool F64, bool WRITE, bool BATCH>
+__global__ void __launch_bounds__(256) k_hub_warp(Plan p, QueryBufs b, int32_t p_hub,
+                                                  const int64_t *__restrict__ row_off)
+{
+    const int32_t qi = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (qi >= p_hub) return;  // uniform per warp
+    if (BATCH) {
+        const int32_t qp = __ldg(b.hub_pos + qi);
+        hub_query<F64, WRITE>(b.plans[__ldg(b.graph_of + qp)], b, qi, qp, row_off);
+    } else {
+        hub_query<F64, WRITE>(p, b, qi, qi, row_off);
+    }
+}
+
+// One chunk (segment k) of a long hub range, by the whole CTA.  The count
+// pass records the chunk's edges (seg_cnt[k]); the write pass reserves that
+// many entries of the row with one atomic and places them by warp.
+template <bool F64, bool WRITE>
+__device__ __forceinline__ void heavy_chunk(const Plan &p, const QueryBufs &b, int32_t k, const int4 sg, int32_t qp,
+                                            const int64_t *__restrict__ row_off, int32_t *s_red, unsigned &n_cand,
+                                            unsigned &n_re, unsigned &n_edge)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int32_t qi = sg.x;
+    const int j = sg.y >> 1;
+    const PMS q = b.pms[qp];
+    const uint64_t Aq = b.A[qp];
+    PMS64 q64{};
+    if (F64) q64 = b.pms64[qp];
+    const uint64_t W = window_halfwidth(p, q, j);
+    int64_t base = 0;
+    int32_t lim = 0;
+    if (WRITE) {
+        // s_red[0]: first entry of this chunk in the row, s_red[1]: entries placed
+        if (threadIdx.x == 0) {
+            const int32_t cnt = b.seg_cnt[k];
+            s_red[0] = b.warp_cnt[qi] + atomicAdd(&b.cursor[qi], cnt);
+            s_red[1] = 0;
+            s_red[2] = cnt;
+        }
+        __syncthreads();
+        base = row_off[q.id] + s_red[0];
+        lim = s_red[2];
+    }
+    int32_t mine = 0;
+    for (int32_t c0 = sg.z; c0 < sg.w; c0 += blockDim.x) {  // uniform trip count per warp
+        const int32_t c = c0 + threadIdx.x;
+        const bool v = c < sg.w && c != qp;
+        uint64_t Ac = 0;
+        PMS pc{};
+        if (v) { Ac = __ldg(b.A + c); pc = b.pms[c]; }
+        const bool e = v && decide_loaded<F64>(p, b, q, q64, Aq, Ac, pc, c, W, n_cand, n_re);
+        if (WRITE) {
+            const unsigned m = __ballot_sync(0xffffffffu, e);
+            if (m) {
+                int32_t off = 0;
+                if (lane == 0) off = atomicAdd(&s_red[1], __popc(m));
+                off = __shfl_sync(0xffffffffu, off, 0) + __popc(m & lt);
+                if (e && off < lim) b.col_out[base + off] = pc.id - p.id_off;
+            }
+        } else {
+            mine += (int)e;
+        }
+    }
+    if (!WRITE) {
+        int32_t d = mine;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) s_red[threadIdx.x >> 5] = d;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
+            b.seg_cnt[k] = t;
+            if (t) atomicAdd(&b.deg[q.id], t);
+            n_edge += t;
+        }
+        __syncthreads();
+    } else {
+        __syncthreads();
+        if (threadIdx.x == 0 && s_red[1] != lim) atomicOr((unsigned long long *)&b.stats[ST_ERR], 1ull);
+        __syncthreads();
     }
 }
 
 // One CTA per chunk of a long hub range.
-template <bool F64, bool WRITE>
+template <bool F64, bool WRITE, bool BATCH>
 __global__ void __launch_bounds__(256) k_hub_heavy(Plan p, QueryBufs b, const int64_t *__restrict__ row_off)
 {
     __shared__ int32_t s_red[8];
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
     const int32_t nseg = min(*((volatile int32_t *)&b.list_cnt[3]), b.heavy_cap);
     unsigned n_cand = 0, n_re = 0, n_edge = 0;
     for (int32_t k = blockIdx.x; k < nseg; k += gridDim.x) {
         const int4 sg = b.heavy[k];
-        const int32_t qp = sg.x;
-        const int j = sg.y >> 1;
-        const PMS q = b.pms[qp];
-        const uint64_t Aq = b.A[qp];
-        PMS64 q64{};
-        if (F64) q64 = b.pms64[qp];
-        const uint64_t W = window_halfwidth(p, q, j);
-        int64_t base = 0;
-        int32_t deg = 0;
-        if (WRITE) {
-            base = row_off[q.id];
-            deg = (int32_t)(row_off[q.id + 1] - base);
-        }
-        int32_t mine = 0;
-        for (int32_t c0 = sg.z; c0 < sg.w; c0 += blockDim.x) {  // uniform trip count per warp
-            const int32_t c = c0 + threadIdx.x;
-            const bool v = c < sg.w && c != qp;
-            uint64_t Ac = 0;
-            PMS pc{};
-            if (v) { Ac = __ldg(b.A + c); pc = b.pms[c]; }
-            const bool e = v && decide_loaded<F64>(p, b, q, q64, Aq, Ac, pc, c, W, n_cand, n_re);
-            if (WRITE) warp_emit(b, qp, base, deg, e, pc.id, lt, lane);
-            else mine += (int)e;
-        }
-        if (!WRITE) {
-            int32_t d = mine;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            if (lane == 0) s_red[threadIdx.x >> 5] = d;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int32_t t = 0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
-                if (t) atomicAdd(&b.deg[q.id], t);
-                n_edge += t;
-            }
-            __syncthreads();
+        if (BATCH) {
+            const int32_t qp = __ldg(b.hub_pos + sg.x);
+            heavy_chunk<F64, WRITE>(b.plans[__ldg(b.graph_of + qp)], b, k, sg, qp, row_off, s_red, n_cand, n_re,
+                                    n_edge);
+        } else {
+            heavy_chunk<F64, WRITE>(p, b, k, sg, sg.x, row_off, s_red, n_cand, n_re, n_edge);
         }
     }
     if (!WRITE) add_stats(b.stats, n_cand, n_re, n_edge);
 }
 
+__device__ __forceinline__ int32_t hub_position(const QueryBufs &b, int32_t qi)
+{
+    return b.hub_pos ? __ldg(b.hub_pos + qi) : qi;
+}
+
 // hub rows are written out of order: every one with two or more entries is sorted
 __global__ void k_hub_classify(QueryBufs b, int32_t p_hub)
 {
-    const int64_t qp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (qp >= p_hub) return;
-    const int32_t id = b.pms[qp].id;
+    const int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (qi >= p_hub) return;
+    const int32_t id = b.pms[hub_position(b, (int32_t)qi)].id;
     const int32_t d = b.deg[id];
     if (d < 2) return;
     const int cls = d <= kWarpRow ? 0 : (d <= kSmemRow ? 1 : 2);
@@ -454,31 +597,76 @@ __global__ void k_hub_classify(QueryBufs b, int32_t p_hub)
 
 __global__ void k_hub_check(QueryBufs b, int32_t p_hub)
 {
-    const int64_t qp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (qp >= p_hub) return;
-    if (b.cursor[qp] != b.deg[b.pms[qp].id]) atomicOr((unsigned long long *)&b.stats[ST_ERR], 1ull);
+    const int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (qi >= p_hub) return;
+    if (b.warp_cnt[qi] + b.cursor[qi] != b.deg[b.pms[hub_position(b, (int32_t)qi)].id])
+        atomicOr((unsigned long long *)&b.stats[ST_ERR], 1ull);
 }
 
 constexpr unsigned kHeavyGrid = 152 * 8;
+
+template <bool F64, bool WRITE, bool BATCH>
+static void hub_launch(const Plan &p, const QueryBufs &b, int32_t p_hub, const int64_t *row_off, cudaStream_t s)
+{
+    const unsigned g = (unsigned)(((int64_t)p_hub * 32 + 255) / 256);
+    k_hub_warp<F64, WRITE, BATCH><<<g, 256, 0, s>>>(p, b, p_hub, row_off);
+    k_hub_heavy<F64, WRITE, BATCH><<<kHeavyGrid, 256, 0, s>>>(p, b, row_off);
+}
+
+template <bool WRITE>
+static void hub_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only, int32_t p_hub, const int64_t *row_off,
+                         cudaStream_t s)
+{
+    const bool batch = b.plans != nullptr;
+    if (fp64_only) {
+        if (batch) hub_launch<true, WRITE, true>(p, b, p_hub, row_off, s);
+        else hub_launch<true, WRITE, false>(p, b, p_hub, row_off, s);
+    } else {
+        if (batch) hub_launch<false, WRITE, true>(p, b, p_hub, row_off, s);
+        else hub_launch<false, WRITE, false>(p, b, p_hub, row_off, s);
+    }
+}
+
+constexpr unsigned kRimWriteGrid = 152 * 16;
+
+static void rim_count_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only, unsigned sectors, cudaStream_t s)
+{
+    const bool batch = b.plans != nullptr;
+    if (fp64_only) {
+        if (batch) k_rim_sector<true, true><<<sectors, 256, 0, s>>>(p, b);
+        else k_rim_sector<true, false><<<sectors, 256, 0, s>>>(p, b);
+    } else {
+        if (batch) k_rim_sector<false, true><<<sectors, 256, 0, s>>>(p, b);
+        else k_rim_sector<false, false><<<sectors, 256, 0, s>>>(p, b);
+    }
+}
+
+static void rim_write_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only, const int64_t *row_off,
+                               int32_t *col_idx, cudaStream_t s)
+{
+    const bool batch = b.plans != nullptr;
+    if (batch) k_rim_copy<true><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
+    else k_rim_copy<false><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
+    if (fp64_only) {
+        if (batch) k_rim_relist<true, true><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
+        else k_rim_relist<true, false><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
+    } else {
+        if (batch) k_rim_relist<false, true><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
+        else k_rim_relist<false, false><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
+    }
+}
 
 }  // namespace
 
 int query_launches(const Plan &p, int32_t p_hub, bool write)
 {
-    return (p_hub > 0 ? 3 : 0) + (p.hub_bands < p.B ? 1 : 0);
+    return (p_hub > 0 ? 3 : 0) + (p.hub_bands < p.B ? (write ? 2 : 1) : 0);
 }
 
 cudaError_t launch_count_hub(const Plan &p, const QueryBufs &b, bool fp64_only, int32_t p_hub, cudaStream_t s)
 {
     if (p_hub <= 0) return cudaSuccess;
-    const unsigned g = (unsigned)(((int64_t)p_hub * 32 + 255) / 256);
-    if (fp64_only) {
-        k_hub_warp<true, false><<<g, 256, 0, s>>>(p, b, p_hub, nullptr);
-        k_hub_heavy<true, false><<<kHeavyGrid, 256, 0, s>>>(p, b, nullptr);
-    } else {
-        k_hub_warp<false, false><<<g, 256, 0, s>>>(p, b, p_hub, nullptr);
-        k_hub_heavy<false, false><<<kHeavyGrid, 256, 0, s>>>(p, b, nullptr);
-    }
+    hub_dispatch<false>(p, b, fp64_only, p_hub, nullptr, s);
     k_hub_classify<<<(unsigned)((p_hub + 255) / 256), 256, 0, s>>>(b, p_hub);
     return cudaGetLastError();
 }
@@ -489,34 +677,26 @@ cudaError_t launch_write_hub(const Plan &p, const QueryBufs &b, bool fp64_only, 
     if (p_hub <= 0) return cudaSuccess;
     QueryBufs bw = b;
     bw.col_out = col_idx;
-    const unsigned g = (unsigned)(((int64_t)p_hub * 32 + 255) / 256);
-    if (fp64_only) {
-        k_hub_warp<true, true><<<g, 256, 0, s>>>(p, bw, p_hub, row_off);
-        k_hub_heavy<true, true><<<kHeavyGrid, 256, 0, s>>>(p, bw, row_off);
-    } else {
-        k_hub_warp<false, true><<<g, 256, 0, s>>>(p, bw, p_hub, row_off);
-        k_hub_heavy<false, true><<<kHeavyGrid, 256, 0, s>>>(p, bw, row_off);
-    }
+    hub_dispatch<true>(p, bw, fp64_only, p_hub, row_off, s);
     k_hub_check<<<(unsigned)((p_hub + 255) / 256), 256, 0, s>>>(bw, p_hub);
     return cudaGetLastError();
 }
 
 cudaError_t launch_count_rim(const Plan &p, const QueryBufs &b, bool fp64_only, cudaStream_t s)
 {
-    if (p.hub_bands >= p.B) return cudaSuccess;
-    const unsigned sectors = 1u << p.sbits;
-    if (fp64_only) k_rim_sector<true, false><<<sectors, 256, 0, s>>>(p, b, nullptr, nullptr);
-    else k_rim_sector<false, false><<<sectors, 256, 0, s>>>(p, b, nullptr, nullptr);
+    if (b.plans == nullptr && p.hub_bands >= p.B) return cudaSuccess;
+    const unsigned sectors = b.plans ? (unsigned)b.n_sectors : 1u << p.sbits;
+    if (sectors == 0) return cudaSuccess;
+    rim_count_dispatch(p, b, fp64_only, sectors, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_write_rim(const Plan &p, const QueryBufs &b, bool fp64_only, const int64_t *row_off,
                              int32_t *col_idx, cudaStream_t s)
 {
-    if (p.hub_bands >= p.B) return cudaSuccess;
-    const unsigned sectors = 1u << p.sbits;
-    if (fp64_only) k_rim_sector<true, true><<<sectors, 256, 0, s>>>(p, b, row_off, col_idx);
-    else k_rim_sector<false, true><<<sectors, 256, 0, s>>>(p, b, row_off, col_idx);
+    if (b.plans == nullptr && p.hub_bands >= p.B) return cudaSuccess;
+    if (b.plans != nullptr && b.n_sectors == 0) return cudaSuccess;
+    rim_write_dispatch(p, b, fp64_only, row_off, col_idx, s);
     return cudaGetLastError();
 }
 

@@ -94,9 +94,18 @@ struct WarpSortSmem {
     uint32_t cnt[kWarpBuckets + 1];
 };
 
+// ids of row `id` lie in [0, n), n of the row's graph in a batch
+__device__ __forceinline__ uint32_t row_range(int64_t n, const int32_t *graph_of, const int64_t *noff, int32_t id)
+{
+    if (!graph_of) return (uint32_t)n;
+    const int g = __ldg(graph_of + id);
+    return (uint32_t)(__ldg(noff + g + 1) - __ldg(noff + g));
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ cnt,
-                                                            int64_t n, const int64_t *__restrict__ row_off,
-                                                            int32_t *col_idx)
+                                                            int64_t n, const int32_t *__restrict__ graph_of,
+                                                            const int64_t *__restrict__ noff,
+                                                            const int64_t *__restrict__ row_off, int32_t *col_idx)
 {
     __shared__ WarpSortSmem sm[kWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -108,7 +117,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__res
     const int d = (int)(row_off[id + 1] - base);
     uint32_t nb = 1;
     while (nb * 4 <= (uint32_t)d && nb < (uint32_t)kWarpBuckets) nb <<= 1;
-    const uint32_t mul = bucket_mul(nb, (uint32_t)n);
+    const uint32_t mul = bucket_mul(nb, row_range(n, graph_of, noff, id));
     int32_t *row = col_idx + base;
     for (uint32_t i = lane; i <= nb; i += 32) S.cnt[i] = 0;
     __syncwarp();
@@ -205,6 +214,8 @@ __device__ void sort_span(SortSmem &S, const int32_t *src, int32_t *dst, int m, 
 
 __global__ void __launch_bounds__(kCtaThreads) k_sort_cta_rows(const int32_t *__restrict__ rows,
                                                                 const int32_t *__restrict__ cnt, int64_t n,
+                                                                const int32_t *__restrict__ graph_of,
+                                                                const int64_t *__restrict__ noff,
                                                                 const int64_t *__restrict__ row_off,
                                                                 int32_t *__restrict__ col_idx)
 {
@@ -215,13 +226,13 @@ __global__ void __launch_bounds__(kCtaThreads) k_sort_cta_rows(const int32_t *__
     const int32_t id = rows[r];
     const int64_t base = row_off[id];
     const int d = (int)(row_off[id + 1] - base);
-    sort_span(S, col_idx + base, col_idx + base, d, 0, (uint32_t)n);
+    sort_span(S, col_idx + base, col_idx + base, d, 0, row_range(n, graph_of, noff, id));
 }
 
 // --------------------------------------------------------------------------
 // Big rows.
 // --------------------------------------------------------------------------
-struct BigRow { int64_t tmp_off; int64_t hist_off; int32_t nbk; int32_t id; int64_t ch_off; };
+struct BigRow { int64_t tmp_off; int64_t hist_off; int32_t nbk; int32_t id; int64_t ch_off; int64_t range; };
 struct Item { int64_t src; int64_t dst; int32_t len; int32_t lo; uint32_t range; int32_t pad; };
 
 constexpr int kBigChunk = 4096;   // entries of a big row one CTA histograms / scatters
@@ -229,7 +240,9 @@ constexpr int kBigSmemBk = 8192;  // id buckets a CTA aggregates in shared memor
 
 // offsets of the big rows' ids (tmp), bucket counters (hist) and chunks: one
 // CTA, chunked prefix sums over the rows
-__global__ void __launch_bounds__(kSetupThreads) k_big_setup(const int32_t *__restrict__ rows, int n_big,
+__global__ void __launch_bounds__(kSetupThreads) k_big_setup(const int32_t *__restrict__ rows, int n_big, int64_t n,
+                                                    const int32_t *__restrict__ graph_of,
+                                                    const int64_t *__restrict__ noff,
                                                     const int64_t *__restrict__ row_off, BigRow *__restrict__ br)
 {
     __shared__ long long s_t[32], s_h[32], s_c[32];
@@ -270,7 +283,8 @@ __global__ void __launch_bounds__(kSetupThreads) k_big_setup(const int32_t *__re
             carry_c = ac;
         }
         __syncthreads();
-        if (k < n_big) br[k] = BigRow{s_t[w] + it - d, s_h[w] + ih - h, nbk, id, s_c[w] + ic - c};
+        if (k < n_big)
+            br[k] = BigRow{s_t[w] + it - d, s_h[w] + ih - h, nbk, id, s_c[w] + ic - c, row_range(n, graph_of, noff, id)};
         __syncthreads();
     }
 }
@@ -311,7 +325,7 @@ __global__ void __launch_bounds__(256) k_big_hist(const BigRow *__restrict__ br,
     BigRow R;
     int64_t base, c0, c1;
     if (!big_chunk(br, n_big, row_off, R, base, c0, c1)) return;
-    const uint32_t mul = bucket_mul((uint32_t)R.nbk, (uint32_t)n);
+    const uint32_t mul = bucket_mul((uint32_t)R.nbk, (uint32_t)R.range);
     int32_t *h = hist + R.hist_off;
     if (R.nbk > kBigSmemBk) {
         for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x)
@@ -339,7 +353,7 @@ __global__ void k_big_scan(const BigRow *__restrict__ br, const int64_t *__restr
     int32_t *h = hist + R.hist_off;
     int32_t *cur = h + R.nbk;
     const int64_t rbase = row_off[R.id];
-    const uint32_t mul = bucket_mul((uint32_t)R.nbk, (uint32_t)n);
+    const uint32_t mul = bucket_mul((uint32_t)R.nbk, (uint32_t)R.range);
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int32_t t0 = 0; t0 < R.nbk; t0 += blockDim.x) {
@@ -357,7 +371,7 @@ __global__ void k_big_scan(const BigRow *__restrict__ br, const int64_t *__restr
             const int32_t st = carry + buf[threadIdx.x] - v;
             cur[i] = st;
             if (v > 0) {
-                const int64_t lo = bucket_lo(i, mul), hi = min(n, bucket_lo(i + 1, mul));
+                const int64_t lo = bucket_lo(i, mul), hi = min(R.range, bucket_lo(i + 1, mul));
                 Item it{R.tmp_off + st, rbase + st, v, (int32_t)lo, (uint32_t)(hi - lo), 0};
                 if (v <= kSmemRow) items[atomicAdd(n_items, 1)] = it;
                 else slow[atomicAdd(n_slow, 1)] = it;
@@ -381,7 +395,7 @@ __global__ void __launch_bounds__(256) k_big_scatter(const BigRow *__restrict__ 
     BigRow R;
     int64_t base, c0, c1;
     if (!big_chunk(br, n_big, row_off, R, base, c0, c1)) return;
-    const uint32_t mul = bucket_mul((uint32_t)R.nbk, (uint32_t)n);
+    const uint32_t mul = bucket_mul((uint32_t)R.nbk, (uint32_t)R.range);
     int32_t *cur = hist + R.hist_off + R.nbk;
     int32_t *t = tmp + R.tmp_off;
     if (R.nbk > kBigSmemBk) {
@@ -478,11 +492,11 @@ cudaError_t launch_sort_rows(const Plan &p, const QueryBufs &b, const int32_t co
         attr = true;
     }
     if (counts[0] > 0)
-        k_sort_warp<<<(unsigned)((counts[0] + kWarps - 1) / kWarps), kSortThreads, 0, s>>>(b.rows[0], b.list_cnt + 0,
-                                                                                        p.n, row_off, col_idx);
+        k_sort_warp<<<(unsigned)((counts[0] + kWarps - 1) / kWarps), kSortThreads, 0, s>>>(
+            b.rows[0], b.list_cnt + 0, p.n, b.graph_of, b.noff, row_off, col_idx);
     if (counts[1] > 0)
-        k_sort_cta_rows<<<(unsigned)counts[1], kCtaThreads, sizeof(SortSmem), s>>>(b.rows[1], b.list_cnt + 1, p.n,
-                                                                                 row_off, col_idx);
+        k_sort_cta_rows<<<(unsigned)counts[1], kCtaThreads, sizeof(SortSmem), s>>>(
+            b.rows[1], b.list_cnt + 1, p.n, b.graph_of, b.noff, row_off, col_idx);
     if (counts[2] > 0) {
         const int n_big = counts[2];
         const int64_t nbk_sum = 2 * (big_total / 4096 + 1) + 2 * (int64_t)n_big;
@@ -498,7 +512,7 @@ cudaError_t launch_sort_rows(const Plan &p, const QueryBufs &b, const int32_t co
         int32_t *ctr = (int32_t *)w;
         cudaMemsetAsync(hist, 0, sizeof(int32_t) * 2 * (size_t)nbk_sum, s);
         cudaMemsetAsync(ctr, 0, 2 * sizeof(int32_t), s);
-        k_big_setup<<<1, kSetupThreads, 0, s>>>(b.rows[2], n_big, row_off, br);
+        k_big_setup<<<1, kSetupThreads, 0, s>>>(b.rows[2], n_big, p.n, b.graph_of, b.noff, row_off, br);
         // chunks: sum over the rows of ceil(d / kBigChunk) <= big_total / kBigChunk + n_big
         const unsigned gc = (unsigned)(big_total / kBigChunk + n_big);
         k_big_hist<<<gc, 256, 0, s>>>(br, n_big, row_off, p.n, col_idx, hist);

@@ -71,3 +71,43 @@ def clustered_points(n: int, R: float, seed: int, clusters: int = 4, spread: flo
     r = R - g.exponential(1.0, size=n)
     r = np.clip(r, 0.0, np.nextafter(R, 0.0))
     return r.astype(np.float64), phi.astype(np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Many small graphs in one call, and a stream of requests of mixed size.
+# ---------------------------------------------------------------------------
+BATCH_COUNT = 4096
+BATCH_DRAW_SEED = 42
+BATCH_KBARS = (4.0, 8.0, 16.0, 32.0)
+
+
+def batch_items(count: int = BATCH_COUNT, draw_seed: int = BATCH_DRAW_SEED, n_lo: float = 1e3, n_hi: float = 1e5,
+                first_seed: int = 1000):
+    """The batched workload: ``count`` independent graphs with n log-uniform
+    in [n_lo, n_hi], alpha uniform in [0.55, 1.5], kbar drawn from
+    {4, 8, 16, 32}, Philox seeds first_seed, first_seed + 1, ...  The
+    per-graph parameters come from numpy's generator seeded with draw_seed.
+    Returns a list of (n, alpha, kbar, seed)."""
+    g = np.random.default_rng(draw_seed)
+    n = np.exp(g.uniform(np.log(n_lo), np.log(n_hi), size=count)).astype(np.int64)
+    alpha = g.uniform(0.55, 1.5, size=count)
+    kbar = np.asarray(BATCH_KBARS)[g.integers(0, len(BATCH_KBARS), size=count)]
+    return [(int(n[k]), float(alpha[k]), float(kbar[k]), first_seed + k) for k in range(count)]
+
+
+SERVE_RATE = 200.0
+SERVE_DRAW_SEED = 7
+
+
+def serving_requests(count: int, rate: float = SERVE_RATE, draw_seed: int = SERVE_DRAW_SEED, n_lo: float = 1e3,
+                     n_hi: float = 3e7, first_seed: int = 10000):
+    """The serving workload: Poisson arrivals at ``rate`` requests/s, n
+    log-uniform in [n_lo, n_hi], alpha uniform in [0.55, 1.5], kbar uniform
+    in [4, 32], seed first_seed + request index.  Returns a list of
+    (arrival_s, n, alpha, kbar, seed)."""
+    g = np.random.default_rng(draw_seed)
+    t = np.cumsum(g.exponential(1.0 / rate, size=count))
+    n = np.exp(g.uniform(np.log(n_lo), np.log(n_hi), size=count)).astype(np.int64)
+    alpha = g.uniform(0.55, 1.5, size=count)
+    kbar = g.uniform(4.0, 32.0, size=count)
+    return [(float(t[k]), int(n[k]), float(alpha[k]), float(kbar[k]), first_seed + k) for k in range(count)]

@@ -278,3 +278,20 @@ def test_error_codes(ctx):
     # the context still works after errors
     g = H.generate(ctx, 1000, 1.0, 5.0, 1)
     assert int(g["row_off"][-1]) == g["col_idx"].numel()
+
+
+# Small graphs: few points per band and wide windows, where a window that
+# wraps through angle 0 can leave its gap inside a single angular bucket.
+SWEEP = [(1500, 0.9, 16.0, 17)] + [
+    (int(800 + 97 * k), 0.55 + 0.05 * (k % 19), (4.0, 8.0, 16.0, 32.0)[k % 4], 100 + k) for k in range(40)]
+
+
+@pytest.mark.parametrize("fp64", [False, True], ids=["fp32filter", "fp64"])
+def test_small_graph_sweep_matches_brute_force(ctx, fp64):
+    for n, alpha, kbar, seed in SWEEP:
+        g = H.generate(ctx, n, alpha, kbar, seed, fp64_only=fp64)
+        R = g["stats"]["R"]
+        r, phi = O.sample(n, alpha, R, seed)
+        o_off, o_col = O.brute_csr(r, phi, R)
+        _, ties = O.brute_ties(r, phi, R)
+        assert_csr_matches(_np(g["row_off"]), _np(g["col_idx"]), o_off, o_col, ties)
