@@ -41,8 +41,9 @@ WORKLOAD = W.LARGE
 # logarithmically with n).
 ORACLE_SAMPLE_N = 2_000_000
 
-# DRAM traffic per launch of the dominant kernel from one ncu capture, valid
-# only while the kernel source hashes to the recorded value.
+# DRAM bytes per point of the dominant kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture at n = 4e6, divided by n), keyed by
+# the hash of the sources it was taken with: a changed kernel reports null.
 NCU_TRAFFIC = {}
 
 
@@ -56,7 +57,7 @@ def peaks():
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("hrg_query.cu", "hrg_common.cuh", "hrg_points.cu"):
+    for f in ("hrg_query.cu", "hrg_common.cuh", "hrg_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1501_03545_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -405,24 +406,22 @@ def main():
                "d2h_bytes_per_step": int(16 * n + 8 * (n + 1) + 4 * ne), "ms_per_step": 1e3 * es}
         del rh, ph, oh, ch
 
-    # roofline of the dominant kernel group
+    # roofline of the dominant kernel: the rim count pass (k_rim_sector), one
+    # launch per graph, timed by the library's CUDA events around exactly that
+    # launch on the job stream
     peak, peak_kind = peaks()
     n = w.n
     stage["count"] = stage["count_hub"] + stage["count_rim"]
     stage["write"] = stage["write_hub"] + stage["write_rim"]
-    kern = max(("count", "write", "rowsort"), key=lambda k: stage[k])
-    algo = {
-        # count pass: candidate structure read once (A 8 B + FP32 data 16 B), degree written (4 B)
-        "count": 24 * n + 4 * n,
-        # write pass: structure read once, offsets + degree read, the CSR neighbour ids written
-        "write": 24 * n + 12 * n + 4 * n_entries,
-        # row sort: every entry of a row longer than 32 read and written once
-        "rowsort": 8 * n_entries,
-    }[kern]
-    achieved = algo / (stage[kern] / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes": algo,
-            "traffic": NCU_TRAFFIC.get((kern, source_hash())),
+    # algorithmic bytes per launch: the band structure read once (fixed-point
+    # angle 8 B + FP32 {P, M, S, id} 16 B per point) and the degree written (4 B)
+    algo = 28 * n
+    achieved = algo / (stage["count_rim"] / 1e3) / 1e9
+    traffic = NCU_TRAFFIC.get(source_hash())
+    roof = {"bound": "hbm", "kernel": "k_rim_sector (rim count pass)", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes": algo,
+            "ms_per_launch": stage["count_rim"],
+            "traffic": None if traffic is None else traffic * n,
             "query_csr_roofline": {
                 "bytes": 4 * n_entries + 8 * (n + 1) + 2 * 16 * n,
                 "ms": stage["count"] + stage["offsets"] + stage["write"] + stage["rowsort"]}}

@@ -170,6 +170,11 @@ extern "C" int hrg_create(hrg_ctx **out, int device)
         delete ctx;
         return HRG_ECUDA;
     }
+    e = upload_log_table();
+    if (e != cudaSuccess) {
+        delete ctx;
+        return HRG_ECUDA;
+    }
     e = cudaMallocHost(&ctx->pinned, 4096);
     if (e != cudaSuccess) {
         delete ctx;
@@ -221,6 +226,8 @@ static void plan_bands(Plan &p, int64_t n, double R, double alpha, int bands)
     p.big = std::cosh(alpha * R) - 1.0;
     p.inv_alpha = 1.0 / alpha;
     p.half_R = 0.5 * R;
+    p.half_R_hi = (float)p.half_R;
+    p.half_R_lo = (float)(p.half_R - (double)p.half_R_hi);
     int B = bands > 0 ? bands : (int)std::ceil(R / 1.5);
     if (B < 1) B = 1;
     if (B > HRG_MAX_BANDS) B = HRG_MAX_BANDS;

@@ -24,6 +24,7 @@ struct Plan {
     double big;          // cosh(alpha R) - 1, the scale of Eq. (1)'s inverse CDF
     double inv_alpha;    // 1 / alpha
     double half_R;       // R / 2
+    float half_R_hi, half_R_lo;  // R / 2 as a float pair (hi + lo)
     double inv_width;    // B / R
     int B;               // number of radial bands
     int hub_bands;       // bands [0, hub_bands) are queried one warp per vertex
@@ -69,14 +70,42 @@ __device__ __forceinline__ U4 philox_block(uint64_t ctr, uint64_t seed)
     return s;
 }
 
+// Natural logarithm of a normal double x >= 1 by the table-driven reduction
+// of P. T. P. Tang (ACM TOMS 16(4), 1990): x = 2^e (F_j + f) with
+// F_j = 1 + j/128 (j = the top 7 mantissa bits) and 0 <= f < 1/128, so
+//   log x = e ln 2 + log F_j + log(1 + t),  t = f / F_j in [0, 2^-7),
+// with log(1 + t) from its Taylor series through t^6/6 (the next term is
+// below 2^-51.8, under 0.1 ulp of any result >= 16).  tab[j] = 1 / F_j and
+// tab[128 + j] = log F_j are tabulated on the host.  ln 2 is split into a
+// 40-bit head (e times it is exact) and the rounded remainder.
+constexpr double kLn2Hi = 0x1.62e42fefa4p-1;
+constexpr double kLn2Lo = -0x1.8432a1b0e2634p-43;
+
+__device__ __forceinline__ double log_table(double x, const double *tab)
+{
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)(bits >> 52) - 1023;
+    const int j = (int)((bits >> 45) & 127);
+    const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+    const double F = __longlong_as_double(0x3FF0000000000000ll | ((long long)j << 45));
+    const double t = (m - F) * tab[j];  // m - F is exact
+    double c = -1.0 / 6.0;
+    c = fma(c, t, 1.0 / 5.0);
+    c = fma(c, t, -1.0 / 4.0);
+    c = fma(c, t, 1.0 / 3.0);
+    c = fma(c, t, -1.0 / 2.0);
+    const double l1p = fma(c * t, t, t);
+    return fma((double)e, kLn2Hi, tab[128 + j]) + fma((double)e, kLn2Lo, l1p);
+}
+
 // Radius of Eq. (1)'s inverse CDF, r = acosh(x) / alpha with x = 1 + u_r
 // (cosh(alpha R) - 1).  For x >= 2^24, acosh(x) = log(2x) - 1/(4x^2) - ...
-// and the dropped terms are below 2^-50 against log(2x) > 17: log alone is
-// exact to well under an ulp there (and skips acosh's square root).
-__device__ __forceinline__ double radius_of(double u_r, double big, double inv_alpha)
+// and the dropped terms are below 2^-50 against log(2x) > 17: the log alone
+// is exact to well under an ulp there (and skips acosh's square root).
+__device__ __forceinline__ double radius_of(double u_r, double big, double inv_alpha, const double *log_tab)
 {
     const double x = __dadd_rn(1.0, __dmul_rn(u_r, big));
-    const double a = x >= 0x1p24 ? log(x + x) : acosh(x);
+    const double a = x >= 0x1p24 ? log_table(x + x, log_tab) : acosh(x);
     return a * inv_alpha;
 }
 
@@ -130,22 +159,33 @@ __device__ __forceinline__ int64_t bucket_of(const Plan &p, int band, uint64_t A
 // ---------------------------------------------------------------------------
 struct __align__(16) PMS { float P, M, S; int32_t id; };
 
-__device__ __forceinline__ float exp_split(double t)
+// a + b = s + e exactly (Knuth's two-sum), in float
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
 {
-    // e^t in float with the argument kept to ~2^-48 relative: t = hi + lo
-    const float hi = (float)t;
-    const float lo = (float)(t - (double)hi);
-    return expf(hi) * (1.0f + lo);
+    const float s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
 }
 
+// e^{r - R/2} and e^{-r - R/2} with their arguments carried as float pairs
+// (r split once into r_hi + r_lo from the double, R/2 split on the host), so
+// the exponent keeps ~2^-40 absolute accuracy with float arithmetic only:
+// e^{t_hi + t_lo} = e^{t_hi} (1 + t_lo) to within t_lo^2.
 __device__ __forceinline__ PMS scaled_exps(const Plan &p, double r, int32_t id)
 {
     PMS o;
-    const double t = r - p.half_R;
-    o.P = exp_split(t);
-    o.M = exp_split(-t - p.R);
+    const float rh = __double2float_rn(r);
+    const float rl = __double2float_rn(r - (double)rh);
+    float e1, e2;
+    const float th = two_sum(rh, -p.half_R_hi, e1);  // r - R/2
+    const float tl = e1 + (rl - p.half_R_lo);
+    o.P = expf(th) * (1.0f + tl);
+    const float mh = two_sum(-rh, -p.half_R_hi, e2);  // -r - R/2
+    const float ml = e2 - (rl + p.half_R_lo);
+    o.M = expf(mh) * (1.0f + ml);
     // S = P (1 - e^{-2r}); expm1f keeps small radii accurate
-    o.S = o.P * (-expm1f(-2.0f * (float)r));
+    o.S = o.P * (-expm1f(-2.0f * rh));
     o.id = id;
     return o;
 }
@@ -249,6 +289,18 @@ __device__ __forceinline__ bool edge_pms64(const Plan &p, const PMS64 &q, const 
 // ---------------------------------------------------------------------------
 constexpr uint64_t kFullCircle = 0xFFFFFFFFFFFFFFFFull;
 
+// ceil(x) as an unsigned 64-bit integer for 0 <= x < 2^64, from two 32-bit
+// conversions (a 64-bit conversion is an order of magnitude slower).  For
+// x < 2^32 the high word is 0; for x >= 2^32, x is a multiple of 2^9, so
+// x - hi 2^32 is exact in float and integral, and hi = floor(x 2^-32) is
+// exact as a float too.
+__device__ __forceinline__ uint64_t float_to_u64_ru(float x)
+{
+    const float xh = floorf(x * 2.3283064365386963e-10f);  // x 2^-32 is exact
+    const float rem = fmaf(-xh, 4294967296.0f, x);
+    return ((uint64_t)__float2uint_rz(xh) << 32) + __float2uint_ru(rem);
+}
+
 __device__ __forceinline__ uint64_t window_halfwidth(const Plan &p, const PMS &q, int band)
 {
     const float Pb = p.Pb[band], Mb = p.Mb[band], Sb = p.Sb[band];
@@ -266,7 +318,7 @@ __device__ __forceinline__ uint64_t window_halfwidth(const Plan &p, const PMS &q
     float th = X <= 0.25f ? 2.0f * sqrtf(X * __frcp_rn(1.0f - X)) : 2.0f * asinf(sqrtf(X));
     th = th * (1.0f + 2e-5f) + 1e-30f;
     if (th >= 3.1415f) return kFullCircle;
-    return __float2ull_ru(th * kAngleScaleUp) + (1ull << 16);
+    return float_to_u64_ru(th * kAngleScaleUp) + (1ull << 16);
 }
 
 }  // namespace hrg

@@ -7,6 +7,8 @@
 namespace hrg {
 
 // ---- points (hrg_points.cu) ----
+// The sampler's table of 1/F_j and log F_j (log_table); once per device.
+cudaError_t upload_log_table();
 // Sampler of Algorithm 1 (angle and radius draws, Eq. (1)): writes r, phi in
 // vertex-id order and the per-band point counts.
 cudaError_t launch_sample(const Plan &p, uint64_t seed, double *r, double *phi, int64_t *band_cnt, cudaStream_t s);

@@ -6,6 +6,8 @@
 // buckets (g chosen so a bucket holds about one point).  A counting sort by
 // (band, bucket) gives every band as a contiguous, angle-bucketed array; the
 // bucket start table doubles as the angular index used by the queries.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include "hrg_internal.h"
 
@@ -14,6 +16,16 @@ namespace hrg {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kSampleGrid = 152 * 16;  // persistent grid of the samplers (each CTA loads the log table once)
+
+// 1/F_j and log F_j, F_j = 1 + j/128 (log_table); filled once per device
+__device__ double g_log_tab[256];
+
+__device__ __forceinline__ void load_log_tab(double *s_tab)
+{
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) s_tab[k] = g_log_tab[k];
+    __syncthreads();
+}
 
 inline int grid_for(int64_t n, int threads, int per_thread = 1)
 {
@@ -38,15 +50,16 @@ __global__ void k_sample(Plan p, uint64_t seed, double *__restrict__ r_out, doub
                          int64_t *__restrict__ band_cnt)
 {
     __shared__ int sh[HRG_MAX_BANDS];
+    __shared__ double s_tab[256];
     for (int k = threadIdx.x; k < HRG_MAX_BANDS; k += blockDim.x) sh[k] = 0;
-    __syncthreads();
+    load_log_tab(s_tab);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
         const U4 w = philox_block((uint64_t)i, seed);
         const double u_phi = unit53(w.x, w.y);
         const double u_r = unit53(w.z, w.w);
         const double phi = __dmul_rn(u_phi, kTwoPi);
-        const double r = radius_of(u_r, p.big, p.inv_alpha);
+        const double r = radius_of(u_r, p.big, p.inv_alpha, s_tab);
         phi_out[i] = phi;
         r_out[i] = r;
         atomicAdd(&sh[band_of(p, r)], 1);
@@ -119,6 +132,8 @@ __global__ void k_graph_of(const Plan *__restrict__ plans, int32_t *__restrict__
 __global__ void k_sample_batch(const Plan *__restrict__ plans, const int32_t *__restrict__ graph_of, int64_t N,
                                double *__restrict__ r_out, double *__restrict__ phi_out)
 {
+    __shared__ double s_tab[256];
+    load_log_tab(s_tab);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
         const Plan &p = plans[__ldg(graph_of + i)];
@@ -126,7 +141,7 @@ __global__ void k_sample_batch(const Plan *__restrict__ plans, const int32_t *__
         const double u_phi = unit53(w.x, w.y);
         const double u_r = unit53(w.z, w.w);
         phi_out[i] = __dmul_rn(u_phi, kTwoPi);
-        r_out[i] = radius_of(u_r, p.big, p.inv_alpha);
+        r_out[i] = radius_of(u_r, p.big, p.inv_alpha, s_tab);
     }
 }
 
@@ -307,7 +322,7 @@ cudaError_t scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t N, void *ws
 
 cudaError_t launch_sample(const Plan &p, uint64_t seed, double *r, double *phi, int64_t *band_cnt, cudaStream_t s)
 {
-    k_sample<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, seed, r, phi, band_cnt);
+    k_sample<<<std::min(grid_for(p.n, kThreads, 4), kSampleGrid), kThreads, 0, s>>>(p, seed, r, phi, band_cnt);
     return cudaGetLastError();
 }
 
@@ -331,6 +346,17 @@ cudaError_t launch_scatter_soa(const Plan &p, const int32_t *gbuf, const int32_t
     return cudaGetLastError();
 }
 
+cudaError_t upload_log_table()
+{
+    double tab[256];
+    for (int j = 0; j < 128; ++j) {
+        const double F = 1.0 + j / 128.0;
+        tab[j] = 1.0 / F;
+        tab[128 + j] = std::log(F);
+    }
+    return cudaMemcpyToSymbol(g_log_tab, tab, sizeof tab);
+}
+
 cudaError_t launch_graph_of(const Plan *plans, int NG, int32_t *graph_of, cudaStream_t s)
 {
     k_graph_of<<<NG, 256, 0, s>>>(plans, graph_of);
@@ -340,7 +366,7 @@ cudaError_t launch_graph_of(const Plan *plans, int NG, int32_t *graph_of, cudaSt
 cudaError_t launch_sample_batch(const Plan *plans, const int32_t *graph_of, int64_t N, double *r, double *phi,
                                 cudaStream_t s)
 {
-    k_sample_batch<<<grid_for(N, kThreads, 4), kThreads, 0, s>>>(plans, graph_of, N, r, phi);
+    k_sample_batch<<<std::min(grid_for(N, kThreads, 4), kSampleGrid), kThreads, 0, s>>>(plans, graph_of, N, r, phi);
     return cudaGetLastError();
 }
 

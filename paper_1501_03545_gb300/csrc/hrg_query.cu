@@ -150,33 +150,10 @@ __device__ __forceinline__ void warp_append(int32_t *list, int32_t *count, bool 
 // One query, one thread (rim bands).  Rows of up to kRegRow entries are kept
 // sorted in registers.  The count pass stores such a row in the row buffer
 // (b.small) and records where (b.small_off[position]); the write pass then
-// copies it instead of traversing the query again (write_stored).  Longer
+// copies it instead of traversing the query again (k_rim_copy).  Longer
 // rows, and rows that did not fit in the buffer, are traversed again by the
 // write pass.
 // ---------------------------------------------------------------------------
-// write pass, row kept by the count pass: sort it in registers and store it;
-// false if the row was not kept
-__device__ __forceinline__ bool write_stored(const Plan &p, const QueryBufs &b, int32_t qp,
-                                             const int64_t *__restrict__ row_off, int32_t *__restrict__ col_idx)
-{
-    const int32_t stored = b.small_off[qp];
-    if (stored < 0) return false;
-    const int32_t id = b.pms[qp].id;
-    const int64_t base = row_off[id];
-    const int32_t deg = (int32_t)(row_off[id + 1] - base);
-    int32_t v[kRegRow];
-#pragma unroll
-    for (int k = 0; k < kRegRow; ++k) v[k] = k < deg ? b.small[stored + k] : 0x7fffffff;
-    if (deg > 16) bitonic_regs<32>(v);
-    else if (deg > 8) bitonic_regs<16>(v);
-    else if (deg > 4) bitonic_regs<8>(v);
-    else if (deg > 1) bitonic_regs<4>(v);
-#pragma unroll
-    for (int k = 0; k < kRegRow; ++k)
-        if (k < deg) col_idx[base + k] = v[k] - p.id_off;
-    return true;
-}
-
 // The traversal.  Count pass: every query of the sector; write pass: only
 // queries whose row was not kept (no warp-collective operations there, so
 // the write pass may call it for any subset of lanes).
@@ -310,16 +287,54 @@ __device__ __forceinline__ void rim_sector(const Plan &p, const QueryBufs &b, in
     add_stats(b.stats, n_cand, n_re, n_edge);
 }
 
-// Write pass of the rim rows.  Kept rows: sort in registers and store.
+// Write pass of the rim rows.  Kept rows: a warp takes 32 of them, loads
+// them row by row (coalesced) into a shared-memory tile, every lane sorts its
+// own row in registers, and the warp stores them row by row.
+constexpr int kCopyWarps = 8;
+
 template <bool BATCH>
-__global__ void __launch_bounds__(256) k_rim_copy(Plan p, QueryBufs b, const int64_t *__restrict__ row_off,
-                                                  int32_t *__restrict__ col_idx)
+__global__ void __launch_bounds__(32 * kCopyWarps) k_rim_copy(Plan p, QueryBufs b, const int64_t *__restrict__ row_off,
+                                                              int32_t *__restrict__ col_idx)
 {
+    __shared__ int32_t tile[kCopyWarps][kRegRow][kRegRow + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t(*T)[kRegRow + 1] = tile[w];
     const int32_t nk = *((volatile int32_t *)&b.list_cnt[4]);
-    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nk; k += gridDim.x * blockDim.x) {
-        const int32_t qp = b.kept[k];
-        if (BATCH) write_stored(b.plans[__ldg(b.graph_of + qp)], b, qp, row_off, col_idx);
-        else write_stored(p, b, qp, row_off, col_idx);
+    const int32_t nwarps = gridDim.x * kCopyWarps;
+    for (int32_t k0 = (blockIdx.x * kCopyWarps + w) * 32; k0 < nk; k0 += nwarps * 32) {
+        const int32_t k = k0 + lane;
+        int32_t stored = 0, deg = 0, off = 0;
+        int64_t base = 0;
+        if (k < nk) {
+            const int32_t qp = b.kept[k];
+            stored = b.small_off[qp];
+            const int32_t id = b.pms[qp].id;
+            base = row_off[id];
+            deg = (int32_t)(row_off[id + 1] - base);
+            off = BATCH ? b.plans[__ldg(b.graph_of + qp)].id_off : p.id_off;
+        }
+        for (int i = 0; i < 32; ++i) {
+            const int32_t si = __shfl_sync(0xffffffffu, stored, i), di = __shfl_sync(0xffffffffu, deg, i);
+            if (lane < di) T[i][lane] = b.small[si + lane];
+        }
+        __syncwarp();
+        int32_t v[kRegRow];
+#pragma unroll
+        for (int j = 0; j < kRegRow; ++j) v[j] = j < deg ? T[lane][j] : 0x7fffffff;
+        if (deg > 16) bitonic_regs<32>(v);
+        else if (deg > 8) bitonic_regs<16>(v);
+        else if (deg > 4) bitonic_regs<8>(v);
+        else if (deg > 1) bitonic_regs<4>(v);
+#pragma unroll
+        for (int j = 0; j < kRegRow; ++j)
+            if (j < deg) T[lane][j] = v[j] - off;
+        __syncwarp();
+        for (int i = 0; i < 32; ++i) {
+            const int64_t bi = __shfl_sync(0xffffffffu, base, i);
+            const int32_t di = __shfl_sync(0xffffffffu, deg, i);
+            if (lane < di) col_idx[bi + lane] = T[i][lane];
+        }
+        __syncwarp();
     }
 }
 
@@ -645,8 +660,8 @@ static void rim_write_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only
                                int32_t *col_idx, cudaStream_t s)
 {
     const bool batch = b.plans != nullptr;
-    if (batch) k_rim_copy<true><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
-    else k_rim_copy<false><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
+    if (batch) k_rim_copy<true><<<kRimWriteGrid, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
+    else k_rim_copy<false><<<kRimWriteGrid, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
     if (fp64_only) {
         if (batch) k_rim_relist<true, true><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
         else k_rim_relist<true, false><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);

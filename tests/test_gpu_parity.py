@@ -96,6 +96,7 @@ def test_scaled_workloads_match_band_oracle(ctx, w, n):
     R = g["stats"]["R"]
     r, phi = O.sample(n, w.alpha, R, w.seed)
     assert np.array_equal(_np(g["phi"]), phi)
+    assert np.all(np.abs(_np(g["r"]) - r) <= 8 * np.spacing(np.maximum(r, 1e-300)))
     b = O.Bands(r, phi, R)
     o_off, o_col = b.csr()
     nt, ties = b.ties()
@@ -109,6 +110,8 @@ def test_medium_workload_full(ctx, fp64):
     R = g["stats"]["R"]
     r, phi = O.sample(w.n, w.alpha, R, w.seed)
     assert np.array_equal(_np(g["phi"]), phi)
+    # radii: acosh below x = 2^24, the table-driven log(2x) above (most points here)
+    assert np.all(np.abs(_np(g["r"]) - r) <= 8 * np.spacing(np.maximum(r, 1e-300)))
     b = O.Bands(r, phi, R)
     o_off, o_col = b.csr()
     nt, ties = b.ties()
@@ -131,6 +134,8 @@ def test_large_workload_sampled_rows(ctx):
     gphi = g["phi"]
     idx = torch.randint(0, n, (1 << 20,), device=gphi.device, generator=torch.Generator(device=gphi.device).manual_seed(5))
     assert np.array_equal(_np(gphi[idx]), phi[_np(idx)])
+    ri = r[_np(idx)]
+    assert np.all(np.abs(_np(g["r"][idx]) - ri) <= 8 * np.spacing(ri))
     hubs = np.argsort(r)[:8]
     rng = np.random.default_rng(7)
     qids = np.concatenate([hubs, rng.integers(0, n, 32)])
