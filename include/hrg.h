@@ -198,6 +198,9 @@ int hrg_generate(hrg_ctx *ctx, const hrg_params *p, void *stream, double *r_out,
  * row_off and col_idx back (r_host double[n], phi_host double[n],
  * row_off_host int64[n+1], col_idx_host int32[col_capacity]).  Host buffers
  * registered with cudaHostRegister (or pinned) copy at full link speed.
+ * The context generates on a stream of its own; r, phi and row_off travel
+ * back on a second one while the neighbour ids are written and sorted.
+ * The call returns when every copy is complete.
  * Errors as hrg_generate.
  */
 int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_host, double *phi_host, int64_t *row_off_host,

@@ -104,10 +104,11 @@ struct hrg_ctx {
     enum { W_BANDCNT, W_GBUF, W_CNT, W_START, W_SLOT, W_A, W_PMS, W_PMS64, W_DEG, W_STATS, W_LIST0, W_LIST1,
            W_LIST2, W_LISTCNT, W_BIGTOT, W_SCAN, W_TMP, W_BUCKET, W_OUT_R, W_OUT_PHI, W_OUT_OFF, W_OUT_COL,
            W_HEAVY, W_CURSOR, W_SMALL, W_SMALLOFF, W_SMALLCUR, W_PLANS, W_NOFF, W_SOFF, W_GRAPHOF, W_HUBCNT,
-           W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_KEPT, W_RELIST, W_COUNT };
+           W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_KEPT0, W_KEPT1, W_KEPT2, W_KEPT3, W_RELIST, W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
     cudaEvent_t ev[10] = {};  // stage boundaries of the current job
+    cudaStream_t work = nullptr, copy = nullptr;  // hrg_generate_host: generation and read-back streams
     hrg_job job;
     std::vector<Plan> batch_plans;  // host plans of the current batch
     std::vector<int64_t> batch_noff, batch_soff;
@@ -198,6 +199,8 @@ extern "C" int hrg_destroy(hrg_ctx *ctx)
     for (auto &b : ctx->ws)
         if (b.ptr) cudaFree(b.ptr);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->work) cudaStreamDestroy(ctx->work);
+    if (ctx->copy) cudaStreamDestroy(ctx->copy);
     for (auto &ev : ctx->ev)
         if (ev) cudaEventDestroy(ev);
     delete ctx;
@@ -308,12 +311,13 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     if ((rc = ensure(ctx, hrg_ctx::W_STATS, sizeof(uint64_t) * 8, &stats))) return rc;
     for (int k = 0; k < 3; ++k)
         if ((rc = ensure(ctx, hrg_ctx::W_LIST0 + k, sizeof(int32_t) * n, &lists[k]))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 8, &listcnt))) return rc;
-    void *kept, *relist;
-    if ((rc = ensure(ctx, hrg_ctx::W_KEPT, sizeof(int32_t) * n, &kept))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_RELIST, sizeof(int32_t) * n, &relist))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 12, &listcnt))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_BIGTOT, sizeof(int64_t), &bigtot))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_workspace_bytes(n), &scanws))) return rc;
+    void *kept[4], *relist;
+    for (int k = 0; k < 4; ++k)
+        if ((rc = ensure(ctx, hrg_ctx::W_KEPT0 + k, sizeof(int32_t) * n, &kept[k]))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_RELIST, sizeof(int32_t) * n, &relist))) return rc;
     const Plan &p = J.plan;
     b.r = J.r;
     b.phi = J.phi;
@@ -321,7 +325,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     b.stats = (unsigned long long *)stats;
     for (int k = 0; k < 3; ++k) b.rows[k] = (int32_t *)lists[k];
     b.list_cnt = (int32_t *)listcnt;
-    b.kept = (int32_t *)kept;
+    for (int k = 0; k < 4; ++k) b.kept[k] = (int32_t *)kept[k];
     b.relist = (int32_t *)relist;
     b.big_total = (int64_t *)bigtot;
     // heavy hub segments (long hub ranges cut into CTA chunks) and hub row cursors
@@ -351,7 +355,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
         b.seg_cnt = (int32_t *)scnt;
         b.heavy_cap = (int32_t)heavy_cap;
         CK(cudaMemsetAsync(stats, 0, sizeof(uint64_t) * 8, st));
-        CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 8, st));
+        CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 12, st));
         CK(cudaMemsetAsync(bigtot, 0, sizeof(int64_t), st));
         CK(cudaMemsetAsync(deg, 0, sizeof(int32_t) * n, st));
         CK(cudaMemsetAsync(small_cur, 0, sizeof(unsigned long long), st));
@@ -427,6 +431,8 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     int64_t cnt_copy[HRG_MAX_BANDS];
     memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
     plan_buckets(p, cnt_copy, &J.p_hub, (prm && prm->hub_candidates > 0) ? (double)prm->hub_candidates : 512.0);
+    // the counts are exact here: queries may skip the empty innermost bands
+    while (p.first_band < p.B - 1 && cnt_copy[p.first_band] == 0) ++p.first_band;
 
     // 2. counting sort by (band, angular bucket)
     void *cnt, *start;
@@ -772,6 +778,8 @@ extern "C" int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_ho
     if (!p || !r_host || !phi_host || !row_off_host || !n_entries) return set_err(ctx, HRG_EINVAL, "null argument");
     if (p->n < 2 || p->n > 0x7fffffffLL) return set_err(ctx, HRG_EINVAL, "n must be in [2, 2^31)");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    if (!ctx->work) CK(cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking));
+    if (!ctx->copy) CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
     const int64_t n = p->n;
     void *dr, *dphi, *doff, *dcol;
     int rc;
@@ -780,7 +788,7 @@ extern "C" int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_ho
     if ((rc = ensure(ctx, hrg_ctx::W_OUT_OFF, sizeof(int64_t) * (n + 1), &doff))) return rc;
     hrg_job *job = nullptr;
     int64_t ne = 0;
-    cudaStream_t st = nullptr;
+    cudaStream_t st = ctx->work, cp = ctx->copy;
     rc = hrg_generate_begin(ctx, p, st, (double *)dr, (double *)dphi, (int64_t *)doff, &job, &ne);
     if (rc) return rc;
     *n_entries = ne;
@@ -794,14 +802,21 @@ extern "C" int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_ho
         hrg_job_release(job);
         return rc;
     }
+    // begin has synchronized the generation stream: the points and row
+    // offsets are final, so they go back to the host while the neighbour
+    // ids are written and sorted
+    CK(cudaMemcpyAsync(r_host, dr, sizeof(double) * n, cudaMemcpyDeviceToHost, cp));
+    CK(cudaMemcpyAsync(phi_host, dphi, sizeof(double) * n, cudaMemcpyDeviceToHost, cp));
+    CK(cudaMemcpyAsync(row_off_host, doff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, cp));
     rc = hrg_generate_finish(job, (int32_t *)dcol);
     if (stats_out) hrg_job_stats(job, stats_out);
     hrg_job_release(job);
-    if (rc) return rc;
-    CK(cudaMemcpyAsync(r_host, dr, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(phi_host, dphi, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(row_off_host, doff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+    if (rc) {
+        cudaStreamSynchronize(cp);
+        return rc;
+    }
     if (ne > 0) CK(cudaMemcpyAsync(col_idx_host, dcol, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    CK(cudaStreamSynchronize(cp));
     return HRG_OK;
 }

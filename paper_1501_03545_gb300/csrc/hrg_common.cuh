@@ -29,6 +29,7 @@ struct Plan {
     int B;               // number of radial bands
     int hub_bands;       // bands [0, hub_bands) are queried one warp per vertex
     int sbits;           // 2^sbits angular sectors; every band has gbits >= sbits
+    int first_band;      // bands below it are known to be empty (0 when the counts are estimates)
     int64_t G;           // total number of angular buckets over all bands
     double band_lo[HRG_MAX_BANDS + 1];  // inner radius of each band; band_lo[B] = +inf
     int64_t base[HRG_MAX_BANDS + 1];    // first bucket of each band; base[B] = G
@@ -319,6 +320,27 @@ __device__ __forceinline__ uint64_t window_halfwidth(const Plan &p, const PMS &q
     th = th * (1.0f + 2e-5f) + 1e-30f;
     if (th >= 3.1415f) return kFullCircle;
     return float_to_u64_ru(th * kAngleScaleUp) + (1ull << 16);
+}
+
+// An upper bound of window_halfwidth over every query whose radius is at
+// least that of q (q at the inner radius of a band beyond `band`): the window
+// shrinks as the query moves out (r_q >= b), X carries an extra 1e-4 relative
+// pad against the FP32 rounding of the two queries' data, and
+// 2 sqrt(X / (1 - X)) >= 2 asin(sqrt X) bounds both of window_halfwidth's
+// branches.
+__device__ __forceinline__ uint64_t window_bound(const Plan &p, const PMS &q, int band)
+{
+    const float Pb = p.Pb[band], Mb = p.Mb[band], Sb = p.Sb[band];
+    const float den = q.S * Sb;
+    if (!(den > 0.0f)) return kFullCircle;
+    const float sub = fmaf(q.P, Mb, Pb * q.M);
+    const float num = p.rhs32 - sub;
+    float X = fmaf(num, 1.0f + 2e-5f, 2e-5f * (1.0f + sub)) / den * (1.0f + 1e-4f);
+    if (X >= 0.999f) return kFullCircle;
+    if (!(X > 0.0f)) X = 0.0f;
+    const float th = 2.0f * sqrtf(X / (1.0f - X)) * (1.0f + 1e-3f) + 1e-30f;
+    if (th >= 3.1415f) return kFullCircle;
+    return float_to_u64_ru(th * kAngleScaleUp) + (1ull << 20);
 }
 
 }  // namespace hrg

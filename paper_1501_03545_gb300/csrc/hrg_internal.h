@@ -62,9 +62,10 @@ struct QueryBufs {
     int32_t *deg;             // [n] id order
     unsigned long long *stats;  // [8] counters: candidates, rechecks, edges, ..., [7] error flag
     int32_t *rows[3];         // ids of rows to sort: (kRegRow, kWarpRow], (kWarpRow, kSmemRow], > kSmemRow
-    int32_t *list_cnt;        // [8] lengths: [0..2] the three sort lists, [3] heavy segments,
-                              //     [4] kept rim rows, [5] rim rows to traverse again
-    int32_t *kept;            // [n] positions of rim queries whose row the count pass kept
+    int32_t *list_cnt;        // [12] lengths: [0..2] the three sort lists, [3] heavy segments,
+                              //     [4..7] kept rim rows by size class, [8] rim rows to traverse again
+    int32_t *kept[4];         // [n] each: positions of rim queries whose row the count pass kept, by
+                              //     size: 1..4, 5..8, 9..16, 17..kRegRow entries
     int32_t *relist;          // [n] positions of rim queries the write pass traverses again
     int64_t *big_total;       // [1] sum of degrees of the longest rows
     int4 *heavy;              // [heavy_cap] (query position, 2*band+part, begin, end) of long hub ranges

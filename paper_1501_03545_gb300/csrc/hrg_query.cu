@@ -29,6 +29,7 @@ namespace {
 enum { ST_CAND = 0, ST_RECHECK = 1, ST_EDGES = 2, ST_ERR = 7 };
 
 
+
 // Candidate positions of a query in band j: up to two ranges [s0,e0) [s1,e1)
 struct Ranges { int32_t s0, e0, s1, e1; uint64_t W; };
 
@@ -147,6 +148,7 @@ __device__ __forceinline__ void warp_append(int32_t *list, int32_t *count, bool 
 }
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
 // One query, one thread (rim bands).  Rows of up to kRegRow entries are kept
 // sorted in registers.  The count pass stores such a row in the row buffer
 // (b.small) and records where (b.small_off[position]); the write pass then
@@ -156,11 +158,13 @@ __device__ __forceinline__ void warp_append(int32_t *list, int32_t *count, bool 
 // ---------------------------------------------------------------------------
 // The traversal.  Count pass: every query of the sector; write pass: only
 // queries whose row was not kept (no warp-collective operations there, so
-// the write pass may call it for any subset of lanes).
+// the write pass may call it for any subset of lanes).  hub_mask clears the
+// bands that hold no point within reach of the query (count pass).
 template <bool F64, bool WRITE>
 __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, int32_t qp, bool active,
-                                             const int64_t *__restrict__ row_off, int32_t *__restrict__ col_idx,
-                                             unsigned &n_cand, unsigned &n_re, unsigned &n_edge)
+                                             uint64_t hub_mask, const int64_t *__restrict__ row_off,
+                                             int32_t *__restrict__ col_idx, unsigned &n_cand, unsigned &n_re,
+                                             unsigned &n_edge)
 {
     const int lane = threadIdx.x & 31;
     PMS q{};
@@ -175,24 +179,12 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
     }
     int32_t buf[kRegRow];
     int32_t cnt = 0;
-    auto edge = [&](int32_t id) {
-        if (WRITE) {
-            if (cnt < kRegRow) {  // insertion into the sorted list (rows not kept)
-                int32_t k = cnt;
-                while (k > 0 && buf[k - 1] > id) { buf[k] = buf[k - 1]; --k; }
-                buf[k] = id;
-            }
-            if (deg > kRegRow && cnt < deg) col_idx[base + cnt] = id - p.id_off;
-        } else if (cnt < kRegRow) {
-            buf[cnt] = id;  // count pass: kept unsorted
-        }
-        ++cnt;
-    };
     if (active) {
         const uint64_t Aq = b.A[qp];
         PMS64 q64{};
         if (F64) q64 = b.pms64[qp];
-        for (int j = 0; j < p.B; ++j) {
+        for (int j = p.first_band; j < p.B; ++j) {  // bands before first_band hold no point
+            if (j < 64 && !((hub_mask >> j) & 1ull)) continue;  // no point of band j within reach
             const Ranges rg = band_ranges(p, b.start, q, Aq, j);
             for (int part = 0; part < 2; ++part) {
                 const int32_t s = part ? rg.s1 : rg.s0, e = part ? rg.e1 : rg.e0;
@@ -201,7 +193,19 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
                     const uint64_t Ac = __ldg(b.A + c);
                     if (rg.W != kFullCircle && !within(Aq, Ac, rg.W)) continue;
                     const PMS cc = b.pms[c];
-                    if (decide_loaded<F64>(p, b, q, q64, Aq, Ac, cc, c, kFullCircle, n_cand, n_re)) edge(cc.id);
+                    if (!decide_loaded<F64>(p, b, q, q64, Aq, Ac, cc, c, kFullCircle, n_cand, n_re)) continue;
+                    const int32_t id = cc.id;
+                    if (WRITE) {
+                        if (cnt < kRegRow) {  // insertion into the sorted list (rows not kept)
+                            int32_t k = cnt;
+                            for (; k > 0 && buf[k - 1] > id; --k) buf[k] = buf[k - 1];
+                            buf[k] = id;
+                        }
+                        if (deg > kRegRow && cnt < deg) col_idx[base + cnt] = id - p.id_off;
+                    } else if (cnt < kRegRow) {
+                        buf[cnt] = id;  // count pass: kept unsorted
+                    }
+                    ++cnt;
                 }
             }
         }
@@ -238,8 +242,10 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
             classify_row(b, q.id, cnt);
         }
         // the write pass's work lists: kept rows, and rows to traverse again
-        warp_append(b.kept, &b.list_cnt[4], active && off >= 0, qp, lane);
-        warp_append(b.relist, &b.list_cnt[5], active && off < 0 && cnt > 0, qp, lane);
+        const int cls = cnt <= 4 ? 0 : (cnt <= 8 ? 1 : (cnt <= 16 ? 2 : 3));
+#pragma unroll
+        for (int c = 0; c < 4; ++c) warp_append(b.kept[c], &b.list_cnt[4 + c], active && off >= 0 && cls == c, qp, lane);
+        warp_append(b.relist, &b.list_cnt[8], active && off < 0 && cnt > 0, qp, lane);
     }
     if (active) n_edge += cnt;
 }
@@ -269,7 +275,37 @@ __device__ __forceinline__ void rim_sector(const Plan &p, const QueryBufs &b, in
         s_pre[0] = 0;
         for (int j = 0; j < HRG_MAX_BANDS; ++j) s_pre[j + 1] += s_pre[j];
     }
+    // Hub bands that the queries of a rim band of this sector can reach: the
+    // sector widened by a bound of their windows (window_bound at the rim
+    // band's inner radius).  A hub band with no point there is skipped by
+    // every query of that rim band.
+    __shared__ unsigned long long s_mask[HRG_MAX_BANDS];
+    const int H = p.hub_bands, NR = p.B - p.hub_bands;
+    for (int t = threadIdx.x; t < HRG_MAX_BANDS; t += blockDim.x) s_mask[t] = ~0ull;
     __syncthreads();
+    if (p.sbits > 0) {
+        for (int t = threadIdx.x; t < NR * H; t += blockDim.x) {
+            const int i = H + t / H, jh = t % H;
+            if (jh < p.first_band) continue;
+            const PMS qi = scaled_exps(p, p.band_lo[i], 0);
+            const uint64_t W = window_bound(p, qi, jh);
+            const int g = p.gbits[jh];
+            const uint64_t span = (1ull << (64 - p.sbits)) - 1;  // the sector is [slo, slo + span]
+            if (W == kFullCircle || g == 0 || W >= (~0ull - span) / 2) continue;
+            const uint64_t slo = (uint64_t)sector << (64 - p.sbits);
+            const uint64_t lo = slo - W, hi = slo + span + W;
+            const int64_t b0 = p.base[jh], G = (int64_t)1 << g;
+            const int64_t bl = (int64_t)(lo >> (64 - g)), bh = (int64_t)(hi >> (64 - g));
+            int32_t pts;
+            if (lo <= hi) pts = __ldg(b.start + b0 + bh + 1) - __ldg(b.start + b0 + bl);
+            else if (bh < bl)
+                pts = (__ldg(b.start + b0 + G) - __ldg(b.start + b0 + bl)) + (__ldg(b.start + b0 + bh + 1) -
+                                                                               __ldg(b.start + b0));
+            else continue;
+            if (pts == 0) atomicAnd(&s_mask[i], ~(1ull << jh));
+        }
+        __syncthreads();
+    }
     const int32_t total = s_pre[HRG_MAX_BANDS];
     unsigned n_cand = 0, n_re = 0, n_edge = 0;
     int j = 0;
@@ -282,31 +318,46 @@ __device__ __forceinline__ void rim_sector(const Plan &p, const QueryBufs &b, in
             while (t >= s_pre[j + 1]) ++j;  // t only grows, so j only moves forward
             qp = s_beg[j] + (t - s_pre[j]);
         }
-        thread_query<F64, false>(p, b, qp, active, nullptr, nullptr, n_cand, n_re, n_edge);
+        thread_query<F64, false>(p, b, qp, active, active ? s_mask[j] : ~0ull, nullptr, nullptr, n_cand, n_re,
+                                 n_edge);
     }
     add_stats(b.stats, n_cand, n_re, n_edge);
 }
 
-// Write pass of the rim rows.  Kept rows: a warp takes 32 of them, loads
-// them row by row (coalesced) into a shared-memory tile, every lane sorts its
-// own row in registers, and the warp stores them row by row.
+// Write pass of the rim rows.  Kept rows: a warp takes 32 of them of one size
+// class (blockIdx.y: up to 4, 8, 16 or 32 entries), loads them row by row
+// (coalesced) into a shared-memory tile, every lane sorts its own row in
+// registers with the class's network, and the warp stores them row by row.
 constexpr int kCopyWarps = 8;
+
+template <int N>
+__device__ __forceinline__ void sort_tile_row(int32_t (*T)[kRegRow + 1], int lane, int32_t deg, int32_t off)
+{
+    int32_t v[kRegRow];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = j < deg ? T[lane][j] : 0x7fffffff;
+    bitonic_regs<N>(v);
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        if (j < deg) T[lane][j] = v[j] - off;
+}
 
 template <bool BATCH>
 __global__ void __launch_bounds__(32 * kCopyWarps) k_rim_copy(Plan p, QueryBufs b, const int64_t *__restrict__ row_off,
                                                               int32_t *__restrict__ col_idx)
 {
     __shared__ int32_t tile[kCopyWarps][kRegRow][kRegRow + 1];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, cls = blockIdx.y;
     int32_t(*T)[kRegRow + 1] = tile[w];
-    const int32_t nk = *((volatile int32_t *)&b.list_cnt[4]);
+    const int32_t nk = *((volatile int32_t *)&b.list_cnt[4 + cls]);
+    const int32_t *kept = b.kept[cls];
     const int32_t nwarps = gridDim.x * kCopyWarps;
     for (int32_t k0 = (blockIdx.x * kCopyWarps + w) * 32; k0 < nk; k0 += nwarps * 32) {
         const int32_t k = k0 + lane;
         int32_t stored = 0, deg = 0, off = 0;
         int64_t base = 0;
         if (k < nk) {
-            const int32_t qp = b.kept[k];
+            const int32_t qp = kept[k];
             stored = b.small_off[qp];
             const int32_t id = b.pms[qp].id;
             base = row_off[id];
@@ -318,16 +369,10 @@ __global__ void __launch_bounds__(32 * kCopyWarps) k_rim_copy(Plan p, QueryBufs 
             if (lane < di) T[i][lane] = b.small[si + lane];
         }
         __syncwarp();
-        int32_t v[kRegRow];
-#pragma unroll
-        for (int j = 0; j < kRegRow; ++j) v[j] = j < deg ? T[lane][j] : 0x7fffffff;
-        if (deg > 16) bitonic_regs<32>(v);
-        else if (deg > 8) bitonic_regs<16>(v);
-        else if (deg > 4) bitonic_regs<8>(v);
-        else if (deg > 1) bitonic_regs<4>(v);
-#pragma unroll
-        for (int j = 0; j < kRegRow; ++j)
-            if (j < deg) T[lane][j] = v[j] - off;
+        if (cls == 0) sort_tile_row<4>(T, lane, deg, off);
+        else if (cls == 1) sort_tile_row<8>(T, lane, deg, off);
+        else if (cls == 2) sort_tile_row<16>(T, lane, deg, off);
+        else sort_tile_row<32>(T, lane, deg, off);
         __syncwarp();
         for (int i = 0; i < 32; ++i) {
             const int64_t bi = __shfl_sync(0xffffffffu, base, i);
@@ -344,15 +389,15 @@ template <bool F64, bool BATCH>
 __global__ void __launch_bounds__(256) k_rim_relist(Plan p, QueryBufs b, const int64_t *__restrict__ row_off,
                                                     int32_t *__restrict__ col_idx)
 {
-    const int32_t nr = *((volatile int32_t *)&b.list_cnt[5]);
+    const int32_t nr = *((volatile int32_t *)&b.list_cnt[8]);
     unsigned n_cand = 0, n_re = 0, n_edge = 0;
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
         const int32_t qp = b.relist[k];
         if (BATCH)
-            thread_query<F64, true>(b.plans[__ldg(b.graph_of + qp)], b, qp, true, row_off, col_idx, n_cand, n_re,
-                                    n_edge);
+            thread_query<F64, true>(b.plans[__ldg(b.graph_of + qp)], b, qp, true, ~0ull, row_off, col_idx, n_cand,
+                                    n_re, n_edge);
         else
-            thread_query<F64, true>(p, b, qp, true, row_off, col_idx, n_cand, n_re, n_edge);
+            thread_query<F64, true>(p, b, qp, true, ~0ull, row_off, col_idx, n_cand, n_re, n_edge);
     }
 }
 
@@ -370,7 +415,7 @@ __device__ __forceinline__ int graph_search(const int64_t *__restrict__ off, int
 // Count pass.  One graph: block x is sector x.  A batch: block x is global
 // sector x; the sector table gives its graph.
 template <bool F64, bool BATCH>
-__global__ void __launch_bounds__(256) k_rim_sector(Plan p, QueryBufs b)
+__global__ void __launch_bounds__(256, 5) k_rim_sector(Plan p, QueryBufs b)
 {
     if (BATCH) {
         const int g = graph_search(b.sec_off, b.NG, blockIdx.x);
@@ -660,8 +705,9 @@ static void rim_write_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only
                                int32_t *col_idx, cudaStream_t s)
 {
     const bool batch = b.plans != nullptr;
-    if (batch) k_rim_copy<true><<<kRimWriteGrid, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
-    else k_rim_copy<false><<<kRimWriteGrid, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
+    const dim3 cg(kRimWriteGrid / 4, 4);
+    if (batch) k_rim_copy<true><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
+    else k_rim_copy<false><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
     if (fp64_only) {
         if (batch) k_rim_relist<true, true><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
         else k_rim_relist<true, false><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
