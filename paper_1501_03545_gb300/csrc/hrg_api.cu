@@ -104,7 +104,8 @@ struct hrg_ctx {
     enum { W_BANDCNT, W_GBUF, W_CNT, W_START, W_SLOT, W_A, W_PMS, W_PMS64, W_DEG, W_STATS, W_LIST0, W_LIST1,
            W_LIST2, W_LISTCNT, W_BIGTOT, W_SCAN, W_TMP, W_BUCKET, W_OUT_R, W_OUT_PHI, W_OUT_OFF, W_OUT_COL,
            W_HEAVY, W_CURSOR, W_SMALL, W_SMALLOFF, W_SMALLCUR, W_PLANS, W_NOFF, W_SOFF, W_GRAPHOF, W_HUBCNT,
-           W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_KEPT0, W_KEPT1, W_KEPT2, W_KEPT3, W_RELIST, W_COUNT };
+           W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_KEPT0, W_KEPT1, W_KEPT2, W_KEPT3, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
+           W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
     cudaEvent_t ev[10] = {};  // stage boundaries of the current job
@@ -231,7 +232,7 @@ static void plan_bands(Plan &p, int64_t n, double R, double alpha, int bands)
     p.half_R = 0.5 * R;
     p.half_R_hi = (float)p.half_R;
     p.half_R_lo = (float)(p.half_R - (double)p.half_R_hi);
-    int B = bands > 0 ? bands : (int)std::ceil(R / 1.5);
+    int B = bands > 0 ? bands : (int)std::ceil(R / 1.7);
     if (B < 1) B = 1;
     if (B > HRG_MAX_BANDS) B = HRG_MAX_BANDS;
     p.B = B;
@@ -314,10 +315,11 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 12, &listcnt))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_BIGTOT, sizeof(int64_t), &bigtot))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_workspace_bytes(n), &scanws))) return rc;
-    void *kept[4], *relist;
-    for (int k = 0; k < 4; ++k)
+    void *kept[4], *relist[4];
+    for (int k = 0; k < 4; ++k) {
         if ((rc = ensure(ctx, hrg_ctx::W_KEPT0 + k, sizeof(int32_t) * n, &kept[k]))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_RELIST, sizeof(int32_t) * n, &relist))) return rc;
+        if ((rc = ensure(ctx, hrg_ctx::W_RELIST0 + k, sizeof(int32_t) * n, &relist[k]))) return rc;
+    }
     const Plan &p = J.plan;
     b.r = J.r;
     b.phi = J.phi;
@@ -326,7 +328,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     for (int k = 0; k < 3; ++k) b.rows[k] = (int32_t *)lists[k];
     b.list_cnt = (int32_t *)listcnt;
     for (int k = 0; k < 4; ++k) b.kept[k] = (int32_t *)kept[k];
-    b.relist = (int32_t *)relist;
+    for (int k = 0; k < 4; ++k) b.relist[k] = (int32_t *)relist[k];
     b.big_total = (int64_t *)bigtot;
     // heavy hub segments (long hub ranges cut into CTA chunks) and hub row cursors
     void *heavy = nullptr, *cursor = nullptr, *wcnt = nullptr, *scnt = nullptr;
@@ -390,6 +392,17 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     return HRG_OK;
 }
 
+static void expected_band_counts(const Plan &p, int64_t *cnt)
+{
+    // radial CDF of Eq. (1): F(r) = (cosh(alpha r) - 1) / (cosh(alpha R) - 1)
+    double prev = 0.0;
+    for (int k = 0; k < p.B; ++k) {
+        const double hi = (k + 1 < p.B) ? (std::cosh(p.alpha * p.band_lo[k + 1]) - 1.0) / p.big : 1.0;
+        cnt[k] = (int64_t)std::llround((double)p.n * std::max(0.0, hi - prev));
+        prev = hi;
+    }
+}
+
 static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params *prm, int64_t n, double R,
                         double alpha, const double *r_in, const double *phi_in, double *r_out, double *phi_out,
                         uint32_t flags, int32_t bands, cudaStream_t st, int64_t *row_off_out, int64_t *n_entries)
@@ -412,36 +425,47 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     if ((rc = ensure(ctx, hrg_ctx::W_PMS, sizeof(PMS) * n, &pms))) return rc;
     if (J.fp64 && (rc = ensure(ctx, hrg_ctx::W_PMS64, sizeof(PMS64) * n, &pms64))) return rc;
 
-    // 1. points and band counts
+    // 1. points.  A sampled graph's band layout is planned from the expected
+    // band counts (Eq. (1)); an injected point set's from its actual counts.
+    const double hub_cand = (prm && prm->hub_candidates > 0) ? (double)prm->hub_candidates : 512.0;
+    int64_t cnt_copy[HRG_MAX_BANDS];
+    int64_t *h_cnt = (int64_t *)ctx->pinned;
     CK(cudaEventRecord(ctx->ev[0], st));
     CK(cudaMemsetAsync(band_cnt, 0, sizeof(int64_t) * HRG_MAX_BANDS, st));
     if (sampled) {
-        CK(launch_sample(p, prm->seed, r_out, phi_out, (int64_t *)band_cnt, st));
+        CK(launch_sample(p, prm->seed, r_out, phi_out, st));
         J.r = r_out;
         J.phi = phi_out;
+        expected_band_counts(p, cnt_copy);
     } else {
         CK(launch_count_bands(p, r_in, phi_in, (int64_t *)band_cnt, st));
         J.r = r_in;
         J.phi = phi_in;
+        CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
     }
     CK(cudaEventRecord(ctx->ev[1], st));
-    int64_t *h_cnt = (int64_t *)ctx->pinned;
-    CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    int64_t cnt_copy[HRG_MAX_BANDS];
-    memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
-    plan_buckets(p, cnt_copy, &J.p_hub, (prm && prm->hub_candidates > 0) ? (double)prm->hub_candidates : 512.0);
-    // the counts are exact here: queries may skip the empty innermost bands
-    while (p.first_band < p.B - 1 && cnt_copy[p.first_band] == 0) ++p.first_band;
+    plan_buckets(p, cnt_copy, &J.p_hub, hub_cand);
 
-    // 2. counting sort by (band, angular bucket)
+    // 2. counting sort by (band, angular bucket); the exact band counts
     void *cnt, *start;
     const size_t scan_bytes = std::max(scan_workspace_bytes(p.G), scan_workspace_bytes(n));
     if ((rc = ensure(ctx, hrg_ctx::W_CNT, sizeof(int32_t) * p.G, &cnt))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_START, sizeof(int32_t) * (p.G + 1), &start))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_bytes, &scanws))) return rc;
     CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * p.G, st));
-    CK(launch_bucket_hist(p, J.r, J.phi, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)cnt, st));
+    CK(launch_bucket_hist(p, J.r, J.phi, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)cnt,
+                          sampled ? (int64_t *)band_cnt : nullptr, st));
+    if (sampled) {
+        CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
+    }
+    // hub queries and empty innermost bands from the exact counts
+    J.p_hub = 0;
+    for (int k = 0; k < p.hub_bands; ++k) J.p_hub += (int32_t)cnt_copy[k];
+    while (p.first_band < p.B - 1 && cnt_copy[p.first_band] == 0) ++p.first_band;
     CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, p.G, scanws, st));
     CK(launch_scatter_soa(p, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, J.r, J.phi, (uint64_t *)A,
                           (PMS *)pms, (PMS64 *)pms64, st));
@@ -519,17 +543,6 @@ extern "C" int hrg_generate_from_points_begin(hrg_ctx *ctx, int64_t n, double R,
 // layout of each graph is planned from the expected band counts of Eq. (1)
 // (n times the radial CDF mass of the band), so planning needs no read-back.
 // ---------------------------------------------------------------------------
-static void expected_band_counts(const Plan &p, int64_t *cnt)
-{
-    // radial CDF of Eq. (1): F(r) = (cosh(alpha r) - 1) / (cosh(alpha R) - 1)
-    double prev = 0.0;
-    for (int k = 0; k < p.B; ++k) {
-        const double hi = (k + 1 < p.B) ? (std::cosh(p.alpha * p.band_lo[k + 1]) - 1.0) / p.big : 1.0;
-        cnt[k] = (int64_t)std::llround((double)p.n * std::max(0.0, hi - prev));
-        prev = hi;
-    }
-}
-
 extern "C" int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_params *items, uint32_t flags,
                                         void *stream, double *r_out, double *phi_out, int64_t *row_off_out,
                                         hrg_job **job, int64_t *n_entries)

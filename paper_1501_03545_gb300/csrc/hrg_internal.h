@@ -10,15 +10,15 @@ namespace hrg {
 // The sampler's table of 1/F_j and log F_j (log_table); once per device.
 cudaError_t upload_log_table();
 // Sampler of Algorithm 1 (angle and radius draws, Eq. (1)): writes r, phi in
-// vertex-id order and the per-band point counts.
-cudaError_t launch_sample(const Plan &p, uint64_t seed, double *r, double *phi, int64_t *band_cnt, cudaStream_t s);
+// vertex-id order.
+cudaError_t launch_sample(const Plan &p, uint64_t seed, double *r, double *phi, cudaStream_t s);
 // Per-band point counts of an injected point set.
 cudaError_t launch_count_bands(const Plan &p, const double *r, const double *phi, int64_t *band_cnt, cudaStream_t s);
 // Angular-bucket id of every point (gbuf, id order), bucket occupancy (cnt)
 // and the point's rank inside its bucket (slot; order inside a bucket is
-// unspecified).
+// unspecified); with band_cnt non-null, also the exact per-band counts.
 cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi, int32_t *gbuf, int32_t *slot,
-                               int32_t *cnt, cudaStream_t s);
+                               int32_t *cnt, int64_t *band_cnt, cudaStream_t s);
 // Structure-of-arrays in bucket order (point i at start[gbuf[i]] + slot[i]):
 // fixed-point angle, FP32 scaled exps + id; optionally the FP64 data of the
 // plain double-precision path.
@@ -63,10 +63,11 @@ struct QueryBufs {
     unsigned long long *stats;  // [8] counters: candidates, rechecks, edges, ..., [7] error flag
     int32_t *rows[3];         // ids of rows to sort: (kRegRow, kWarpRow], (kWarpRow, kSmemRow], > kSmemRow
     int32_t *list_cnt;        // [12] lengths: [0..2] the three sort lists, [3] heavy segments,
-                              //     [4..7] kept rim rows by size class, [8] rim rows to traverse again
+                              //     [4..7] kept rim rows by size class, [8..11] rim rows to traverse again
     int32_t *kept[4];         // [n] each: positions of rim queries whose row the count pass kept, by
                               //     size: 1..4, 5..8, 9..16, 17..kRegRow entries
-    int32_t *relist;          // [n] positions of rim queries the write pass traverses again
+    int32_t *relist[4];       // [n] each: positions of rim queries the write pass traverses again, by
+                              //     length: up to 64, 128, 256 entries, longer
     int64_t *big_total;       // [1] sum of degrees of the longest rows
     int4 *heavy;              // [heavy_cap] (query position, 2*band+part, begin, end) of long hub ranges
     int32_t heavy_cap;

@@ -245,7 +245,11 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
         const int cls = cnt <= 4 ? 0 : (cnt <= 8 ? 1 : (cnt <= 16 ? 2 : 3));
 #pragma unroll
         for (int c = 0; c < 4; ++c) warp_append(b.kept[c], &b.list_cnt[4 + c], active && off >= 0 && cls == c, qp, lane);
-        warp_append(b.relist, &b.list_cnt[8], active && off < 0 && cnt > 0, qp, lane);
+        // rows to traverse again, by length (a warp then walks rows of similar length)
+        const int rc = cnt <= 64 ? 0 : (cnt <= 128 ? 1 : (cnt <= 256 ? 2 : 3));
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            warp_append(b.relist[c], &b.list_cnt[8 + c], active && off < 0 && cnt > 0 && rc == c, qp, lane);
     }
     if (active) n_edge += cnt;
 }
@@ -389,10 +393,12 @@ template <bool F64, bool BATCH>
 __global__ void __launch_bounds__(256) k_rim_relist(Plan p, QueryBufs b, const int64_t *__restrict__ row_off,
                                                     int32_t *__restrict__ col_idx)
 {
-    const int32_t nr = *((volatile int32_t *)&b.list_cnt[8]);
+    const int cls = blockIdx.y;
+    const int32_t nr = *((volatile int32_t *)&b.list_cnt[8 + cls]);
+    const int32_t *relist = b.relist[cls];
     unsigned n_cand = 0, n_re = 0, n_edge = 0;
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
-        const int32_t qp = b.relist[k];
+        const int32_t qp = relist[k];
         if (BATCH)
             thread_query<F64, true>(b.plans[__ldg(b.graph_of + qp)], b, qp, true, ~0ull, row_off, col_idx, n_cand,
                                     n_re, n_edge);
@@ -709,11 +715,11 @@ static void rim_write_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only
     if (batch) k_rim_copy<true><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
     else k_rim_copy<false><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
     if (fp64_only) {
-        if (batch) k_rim_relist<true, true><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
-        else k_rim_relist<true, false><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
+        if (batch) k_rim_relist<true, true><<<dim3(kRimWriteGrid / 4, 4), 256, 0, s>>>(p, b, row_off, col_idx);
+        else k_rim_relist<true, false><<<dim3(kRimWriteGrid / 4, 4), 256, 0, s>>>(p, b, row_off, col_idx);
     } else {
-        if (batch) k_rim_relist<false, true><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
-        else k_rim_relist<false, false><<<kRimWriteGrid, 256, 0, s>>>(p, b, row_off, col_idx);
+        if (batch) k_rim_relist<false, true><<<dim3(kRimWriteGrid / 4, 4), 256, 0, s>>>(p, b, row_off, col_idx);
+        else k_rim_relist<false, false><<<dim3(kRimWriteGrid / 4, 4), 256, 0, s>>>(p, b, row_off, col_idx);
     }
 }
 
