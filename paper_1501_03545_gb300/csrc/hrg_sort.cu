@@ -3,7 +3,8 @@
 // The query traversal emits a row's neighbours in (band, angle) order.  The
 // canonical CSR lists each row ascending, so rows longer than kRegRow (sorted
 // in registers by the query itself) are sorted here:
-//   * kRegRow < d <= kWarpRow:  one warp per row, bucket sort in the warp's
+//   * kRegRow < d <= kWarpRow:  one warp per row; up to 64 ids by a bitonic
+//     network in the warp's registers, more by a bucket sort in the warp's
 //     shared-memory slice (the ids of a row are spread evenly over [0, n), so
 //     d/4 .. d/2 equal-width value buckets hold 2..4 ids each);
 //   * kWarpRow < d <= kSmemRow: one CTA per row, the same bucket sort over
@@ -102,6 +103,35 @@ __device__ __forceinline__ uint32_t row_range(int64_t n, const int32_t *graph_of
     return (uint32_t)(__ldg(noff + g + 1) - __ldg(noff + g));
 }
 
+// Rows of up to 64 ids: a bitonic network over the warp's registers, element
+// i in lane i mod 32 (register a for i < 32, b for i >= 32); partners j < 32
+// apart are exchanged by shuffles, the pair 32 apart inside a lane.  The
+// lower index of a pair keeps the minimum when its block sorts ascending.
+__device__ __forceinline__ void warp_sort64(int32_t *row, int d, int lane)
+{
+    int32_t a = lane < d ? row[lane] : 0x7fffffff;
+    int32_t b = lane + 32 < d ? row[lane + 32] : 0x7fffffff;
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 32) {  // k = 64: every block ascending
+                const int32_t lo = min(a, b), hi = max(a, b);
+                a = lo;
+                b = hi;
+            } else {
+                const int32_t pa = __shfl_xor_sync(0xffffffffu, a, j), pb = __shfl_xor_sync(0xffffffffu, b, j);
+                const bool lower = (lane & j) == 0;
+                const bool up_a = (lane & k) == 0, up_b = ((lane + 32) & k) == 0;
+                a = (lower == up_a) ? min(a, pa) : max(a, pa);
+                b = (lower == up_b) ? min(b, pb) : max(b, pb);
+            }
+        }
+    }
+    if (lane < d) row[lane] = a;
+    if (lane + 32 < d) row[lane + 32] = b;
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ cnt,
                                                             int64_t n, const int32_t *__restrict__ graph_of,
                                                             const int64_t *__restrict__ noff,
@@ -115,10 +145,14 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__res
     const int32_t id = rows[r];
     const int64_t base = row_off[id];
     const int d = (int)(row_off[id + 1] - base);
+    int32_t *row = col_idx + base;
+    if (d <= 64) {  // uniform per warp
+        warp_sort64(row, d, lane);
+        return;
+    }
     uint32_t nb = 1;
     while (nb * 4 <= (uint32_t)d && nb < (uint32_t)kWarpBuckets) nb <<= 1;
     const uint32_t mul = bucket_mul(nb, row_range(n, graph_of, noff, id));
-    int32_t *row = col_idx + base;
     for (uint32_t i = lane; i <= nb; i += 32) S.cnt[i] = 0;
     __syncwarp();
     for (int i = lane; i < d; i += 32) atomicAdd(&S.cnt[__umulhi((uint32_t)row[i], mul)], 1u);
