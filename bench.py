@@ -376,7 +376,8 @@ def main():
 
         items = W.batch_items()
         table = autotune.tune(ctx, items, stream=stream)
-        tuned = autotune.apply(items, table)
+        tuned = H.BatchItems(autotune.apply(items, table))
+        untuned = H.BatchItems(items)
 
         def time_batch(its):
             g = H.generate_batch(ctx, its, stream=stream)
@@ -396,7 +397,7 @@ def main():
             return a.elapsed_time(b) / args.batch_steps, ent, nl
 
         bms, bent, bl = time_batch(tuned)
-        dms, _, _ = time_batch(items)
+        dms, _, _ = time_batch(untuned)
         batched = {"graphs_per_s": len(items) / (bms / 1e3), "entries_per_s": bent / (bms / 1e3),
                    "ms_per_batch": bms, "graphs": len(items), "sum_n": sum(it[0] for it in items),
                    "entries_per_batch": bent, "launches_per_batch": bl,

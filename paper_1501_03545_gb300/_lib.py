@@ -206,33 +206,45 @@ def generate(ctx: Context, n, alpha, avg_degree, seed, R_override=0.0, fp64_only
     return {"r": r, "phi": phi, "row_off": off, "col_idx": col[: ne.value], "stats": s.as_dict()}
 
 
-def generate_batch(ctx: Context, items, fp64_only=False, stream=None):
-    """hrg_generate_batch_begin + hrg_generate_finish: items is a sequence of
+class BatchItems:
+    """The hrg_params array of a batch, built once: items is a sequence of
     (n, alpha, avg_degree, seed) or dicts with those keys (plus optional
-    R_override, bands, hub_candidates).  Returns the concatenated outputs
-    (r, phi, row_off global, col_idx with local ids), the graph offsets
+    R_override, bands, hub_candidates)."""
+
+    def __init__(self, items):
+        self.arr = (hrg_params * len(items))()
+        self.goff = [0]
+        for k, it in enumerate(items):
+            if isinstance(it, dict):
+                self.arr[k] = params(it["n"], it["alpha"], it["avg_degree"], it["seed"], it.get("R_override", 0.0),
+                                     False, it.get("bands", 0), it.get("hub_candidates", 0))
+            else:
+                self.arr[k] = params(*it)
+            self.goff.append(self.goff[-1] + int(self.arr[k].n))
+
+    def __len__(self):
+        return len(self.arr)
+
+
+def generate_batch(ctx: Context, items, fp64_only=False, stream=None):
+    """hrg_generate_batch_begin + hrg_generate_finish on items (a sequence as
+    in BatchItems, or a BatchItems).  Returns the concatenated outputs (r,
+    phi, row_off global, col_idx with local ids), the graph offsets
     goff[count+1] (host list) and stats."""
     import torch
 
     L = load()
     dev = torch.device("cuda", ctx.device)
     st = stream if stream is not None else torch.cuda.current_stream(dev)
-    arr = (hrg_params * len(items))()
-    goff = [0]
-    for k, it in enumerate(items):
-        if isinstance(it, dict):
-            arr[k] = params(it["n"], it["alpha"], it["avg_degree"], it["seed"], it.get("R_override", 0.0), False,
-                            it.get("bands", 0), it.get("hub_candidates", 0))
-        else:
-            arr[k] = params(*it)
-        goff.append(goff[-1] + int(arr[k].n))
+    prepared = items if isinstance(items, BatchItems) else BatchItems(items)
+    arr, goff = prepared.arr, prepared.goff
     N = goff[-1]
     r = torch.empty(N, dtype=torch.float64, device=dev)
     phi = torch.empty(N, dtype=torch.float64, device=dev)
     off = torch.empty(N + 1, dtype=torch.int64, device=dev)
     job = _P()
     ne = ctypes.c_int64()
-    ctx.check(L.hrg_generate_batch_begin(ctx.h, len(items), arr, HRG_FLAG_FP64_ONLY if fp64_only else 0,
+    ctx.check(L.hrg_generate_batch_begin(ctx.h, len(arr), arr, HRG_FLAG_FP64_ONLY if fp64_only else 0,
                                          _P(st.cuda_stream), _P(_dptr(r)), _P(_dptr(phi)), _P(_dptr(off)),
                                          ctypes.byref(job), ctypes.byref(ne)))
     try:

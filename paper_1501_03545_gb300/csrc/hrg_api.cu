@@ -1,9 +1,11 @@
 // hrg_api.cu -- the C ABI (include/hrg.h): contexts, jobs, workspace, plan.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/hrg.h"
@@ -36,18 +38,19 @@ extern "C" int hrg_solve_radius(int64_t n, double alpha, double avg_degree, doub
     if (!R_out || n < 2 || !(alpha > 0.5) || !(avg_degree > 0.0) || !(avg_degree < (double)(n - 1)))
         return HRG_EINVAL;
     const double nn = (double)n;
-    // coarse scan for the maximum on (0, 24]
+    // coarse scan for the maximum on (0, 24], then golden-section search in
+    // the two cells around the best point
     double best = -1e300, at = 0.0;
-    for (int i = 1; i <= 2400; ++i) {
-        const double R = 0.01 * i;
+    for (int i = 1; i <= 96; ++i) {
+        const double R = 0.25 * i;
         const double k = eq22(nn, alpha, R);
         if (k > best) { best = k; at = R; }
     }
-    double a = std::max(0.0, at - 0.01), b = at + 0.01;
+    double a = std::max(0.0, at - 0.25), b = at + 0.25;
     const double gr = 0.6180339887498949;
     double x1 = b - gr * (b - a), x2 = a + gr * (b - a);
     double f1 = eq22(nn, alpha, x1), f2 = eq22(nn, alpha, x2);
-    for (int it = 0; it < 120; ++it) {
+    for (int it = 0; it < 90; ++it) {
         if (f1 < f2) { a = x1; x1 = x2; f1 = f2; x2 = a + gr * (b - a); f2 = eq22(nn, alpha, x2); }
         else { b = x2; x2 = x1; f2 = f1; x1 = b - gr * (b - a); f1 = eq22(nn, alpha, x1); }
     }
@@ -104,7 +107,7 @@ struct hrg_ctx {
     enum { W_BANDCNT, W_GBUF, W_CNT, W_START, W_SLOT, W_A, W_PMS, W_PMS64, W_DEG, W_STATS, W_LIST0, W_LIST1,
            W_LIST2, W_LISTCNT, W_BIGTOT, W_SCAN, W_TMP, W_BUCKET, W_OUT_R, W_OUT_PHI, W_OUT_OFF, W_OUT_COL,
            W_HEAVY, W_CURSOR, W_SMALL, W_SMALLOFF, W_SMALLCUR, W_PLANS, W_NOFF, W_SOFF, W_GRAPHOF, W_HUBCNT,
-           W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_KEPT0, W_KEPT1, W_KEPT2, W_KEPT3, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
+           W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_KEPT0, W_KEPT1, W_KEPT2, W_KEPT3, W_KEPT4, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
            W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
@@ -312,14 +315,14 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     if ((rc = ensure(ctx, hrg_ctx::W_STATS, sizeof(uint64_t) * 8, &stats))) return rc;
     for (int k = 0; k < 3; ++k)
         if ((rc = ensure(ctx, hrg_ctx::W_LIST0 + k, sizeof(int32_t) * n, &lists[k]))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 12, &listcnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 16, &listcnt))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_BIGTOT, sizeof(int64_t), &bigtot))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_workspace_bytes(n), &scanws))) return rc;
-    void *kept[4], *relist[4];
-    for (int k = 0; k < 4; ++k) {
+    void *kept[5], *relist[4];
+    for (int k = 0; k < 5; ++k)
         if ((rc = ensure(ctx, hrg_ctx::W_KEPT0 + k, sizeof(int32_t) * n, &kept[k]))) return rc;
+    for (int k = 0; k < 4; ++k)
         if ((rc = ensure(ctx, hrg_ctx::W_RELIST0 + k, sizeof(int32_t) * n, &relist[k]))) return rc;
-    }
     const Plan &p = J.plan;
     b.r = J.r;
     b.phi = J.phi;
@@ -327,7 +330,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     b.stats = (unsigned long long *)stats;
     for (int k = 0; k < 3; ++k) b.rows[k] = (int32_t *)lists[k];
     b.list_cnt = (int32_t *)listcnt;
-    for (int k = 0; k < 4; ++k) b.kept[k] = (int32_t *)kept[k];
+    for (int k = 0; k < 5; ++k) b.kept[k] = (int32_t *)kept[k];
     for (int k = 0; k < 4; ++k) b.relist[k] = (int32_t *)relist[k];
     b.big_total = (int64_t *)bigtot;
     // heavy hub segments (long hub ranges cut into CTA chunks) and hub row cursors
@@ -339,9 +342,10 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     }
     b.cursor = (int32_t *)cursor;
     b.warp_cnt = (int32_t *)wcnt;
-    // rim rows of up to 32 entries kept by the count pass (about 8 entries per vertex)
+    // rim rows of up to kKeepRow entries kept by the count pass (room for 16
+    // entries per vertex; rows that find none are traversed again)
     void *small = nullptr, *small_off = nullptr, *small_cur = nullptr;
-    const int64_t small_cap = std::min<int64_t>(8 * n + 1024, 0x7fff0000LL);
+    const int64_t small_cap = std::min<int64_t>(16 * n + 1024, 0x7fff0000LL);
     if ((rc = ensure(ctx, hrg_ctx::W_SMALL, sizeof(int32_t) * small_cap, &small))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SMALLOFF, sizeof(int32_t) * n, &small_off))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SMALLCUR, sizeof(unsigned long long), &small_cur))) return rc;
@@ -357,7 +361,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
         b.seg_cnt = (int32_t *)scnt;
         b.heavy_cap = (int32_t)heavy_cap;
         CK(cudaMemsetAsync(stats, 0, sizeof(uint64_t) * 8, st));
-        CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 12, st));
+        CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 16, st));
         CK(cudaMemsetAsync(bigtot, 0, sizeof(int64_t), st));
         CK(cudaMemsetAsync(deg, 0, sizeof(int32_t) * n, st));
         CK(cudaMemsetAsync(small_cur, 0, sizeof(unsigned long long), st));
@@ -457,19 +461,19 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * p.G, st));
     CK(launch_bucket_hist(p, J.r, J.phi, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)cnt,
                           sampled ? (int64_t *)band_cnt : nullptr, st));
-    if (sampled) {
-        CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
-    }
-    // hub queries and empty innermost bands from the exact counts
-    J.p_hub = 0;
-    for (int k = 0; k < p.hub_bands; ++k) J.p_hub += (int32_t)cnt_copy[k];
-    while (p.first_band < p.B - 1 && cnt_copy[p.first_band] == 0) ++p.first_band;
-    CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, p.G, scanws, st));
+    if (sampled) CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));    CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, p.G, scanws, st));
     CK(launch_scatter_soa(p, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, J.r, J.phi, (uint64_t *)A,
                           (PMS *)pms, (PMS64 *)pms64, st));
     CK(cudaEventRecord(ctx->ev[2], st));
+    // the exact band counts (read back behind the scan and the scatter): hub
+    // queries and empty innermost bands
+    if (sampled) {
+        CK(cudaStreamSynchronize(st));
+        memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
+    }
+    J.p_hub = 0;
+    for (int k = 0; k < p.hub_bands; ++k) J.p_hub += (int32_t)cnt_copy[k];
+    while (p.first_band < p.B - 1 && cnt_copy[p.first_band] == 0) ++p.first_band;
 
     // 3. degrees, 4. row offsets
     QueryBufs &b = J.qb;
@@ -567,19 +571,49 @@ extern "C" int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_p
     plans.resize(count);
     noff.assign(count + 1, 0);
     soff.assign(count + 1, 0);
+    // each graph's own plan, in parallel over host threads (the radius solve
+    // and the band layout are independent per graph)
+    std::vector<double> radius(count, 0.0);
+    std::vector<char> bad(count, 0);
+    auto plan_range = [&](int32_t g0, int32_t g1) {
+        for (int32_t g = g0; g < g1; ++g) {
+            const hrg_params &it = items[g];
+            double R = it.R_override;
+            if (it.n < 2 || it.n > 0x7fffffffLL || !(it.alpha > 0.5) || it.bands < 0 || it.bands > HRG_MAX_BANDS ||
+                (!(R > 0.0) && hrg_solve_radius(it.n, it.alpha, it.avg_degree, &R) != HRG_OK)) {
+                bad[g] = 1;
+                continue;
+            }
+            radius[g] = R;
+            Plan &p = plans[g];
+            plan_bands(p, it.n, R, it.alpha, it.bands);
+            int64_t cnt[HRG_MAX_BANDS];
+            expected_band_counts(p, cnt);
+            int32_t ph = 0;
+            plan_buckets(p, cnt, &ph, it.hub_candidates > 0 ? (double)it.hub_candidates : 512.0);
+        }
+    };
+    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)std::thread::hardware_concurrency(), 32,
+                                                                 (int64_t)count / 64 + 1}));
+    if (nt == 1) {
+        plan_range(0, count);
+    } else {
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nt; ++t)
+            pool.emplace_back(plan_range, (int32_t)((int64_t)count * t / nt), (int32_t)((int64_t)count * (t + 1) / nt));
+        for (auto &th : pool) th.join();
+    }
+    // the batch layout, in order
     int64_t N = 0, G = 0, S = 0;
     bool fp64 = (flags & HRG_FLAG_FP64_ONLY) != 0;
     for (int32_t g = 0; g < count; ++g) {
-        double R;
-        int rc = check_params(ctx, &items[g], &R);
-        if (rc) return set_err(ctx, rc, "item %d: %s", g, ctx->err.c_str());
-        fp64 = fp64 || R > 80.0;
+        if (bad[g]) {
+            double R;
+            const int rc = check_params(ctx, &items[g], &R);
+            return set_err(ctx, rc ? rc : HRG_EINVAL, "item %d: %s", g, ctx->err.c_str());
+        }
+        fp64 = fp64 || radius[g] > 80.0;
         Plan &p = plans[g];
-        plan_bands(p, items[g].n, R, items[g].alpha, items[g].bands);
-        int64_t cnt[HRG_MAX_BANDS];
-        expected_band_counts(p, cnt);
-        int32_t ph = 0;
-        plan_buckets(p, cnt, &ph, items[g].hub_candidates > 0 ? (double)items[g].hub_candidates : 512.0);
         noff[g] = N;
         soff[g] = S;
         p.id_off = (int32_t)N;

@@ -48,7 +48,8 @@ cudaError_t scan_i32_to_i32(const int32_t *in, int32_t *out, int64_t N, void *ws
 cudaError_t scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t N, void *ws, cudaStream_t s);
 
 // ---- queries (hrg_query.cu) and row sorts (hrg_sort.cu) ----
-constexpr int kRegRow = 32;       // rows up to this are sorted in registers by the query
+constexpr int kRegRow = 32;       // rows up to this are sorted in registers by the write pass
+constexpr int kKeepRow = 64;      // rows up to this are kept by the count pass (no second traversal)
 constexpr int kWarpRow = 1024;    // rows up to this: one warp, bucket sort in shared memory
 constexpr int kSmemRow = 12288;   // rows up to this: one CTA, bucket sort in shared memory
 
@@ -62,10 +63,10 @@ struct QueryBufs {
     int32_t *deg;             // [n] id order
     unsigned long long *stats;  // [8] counters: candidates, rechecks, edges, ..., [7] error flag
     int32_t *rows[3];         // ids of rows to sort: (kRegRow, kWarpRow], (kWarpRow, kSmemRow], > kSmemRow
-    int32_t *list_cnt;        // [12] lengths: [0..2] the three sort lists, [3] heavy segments,
-                              //     [4..7] kept rim rows by size class, [8..11] rim rows to traverse again
-    int32_t *kept[4];         // [n] each: positions of rim queries whose row the count pass kept, by
-                              //     size: 1..4, 5..8, 9..16, 17..kRegRow entries
+    int32_t *list_cnt;        // [16] lengths: [0..2] the three sort lists, [3] heavy segments,
+                              //     [4..8] kept rim rows by size class, [9..12] rim rows to traverse again
+    int32_t *kept[5];         // [n] each: positions of rim queries whose row the count pass kept, by
+                              //     size: 1..4, 5..8, 9..16, 17..kRegRow, kRegRow+1..kKeepRow entries
     int32_t *relist[4];       // [n] each: positions of rim queries the write pass traverses again, by
                               //     length: up to 64, 128, 256 entries, longer
     int64_t *big_total;       // [1] sum of degrees of the longest rows
@@ -75,7 +76,7 @@ struct QueryBufs {
     int32_t *warp_cnt;        // [p_hub] entries a hub query's own warp found (count pass)
     int32_t *seg_cnt;         // [heavy_cap] entries found in each heavy segment (count pass)
     int32_t *col_out;         // CSR neighbour ids being written (write pass only)
-    int32_t *small;           // [small_cap] sorted rim rows of up to kRegRow entries kept by the count pass
+    int32_t *small;           // [small_cap] rim rows of up to kKeepRow entries kept by the count pass
     int32_t *small_off;       // [n] by position: start of the kept row in small, -1 if not kept
     unsigned long long *small_cursor;  // [1] bump allocator over small
     int64_t small_cap;

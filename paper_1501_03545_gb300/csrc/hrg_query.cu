@@ -177,7 +177,7 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
             deg = (int32_t)(row_off[q.id + 1] - base);
         }
     }
-    int32_t buf[kRegRow];
+    int32_t buf[kKeepRow];
     int32_t cnt = 0;
     if (active) {
         const uint64_t Aq = b.A[qp];
@@ -202,7 +202,7 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
                             buf[k] = id;
                         }
                         if (deg > kRegRow && cnt < deg) col_idx[base + cnt] = id - p.id_off;
-                    } else if (cnt < kRegRow) {
+                    } else if (cnt < kKeepRow) {
                         buf[cnt] = id;  // count pass: kept unsorted
                     }
                     ++cnt;
@@ -217,8 +217,8 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
                 for (int32_t k = 0; k < cnt && k < deg; ++k) col_idx[base + k] = buf[k] - p.id_off;
         }
     } else {
-        // keep rows of up to kRegRow entries: warp-aggregated reservation in b.small
-        const bool keep = active && cnt <= kRegRow && cnt > 0;
+        // keep rows of up to kKeepRow entries: warp-aggregated reservation in b.small
+        const bool keep = active && cnt <= kKeepRow && cnt > 0;
         int32_t want = keep ? cnt : 0;
         int32_t incl = want;
 #pragma unroll
@@ -242,14 +242,14 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
             classify_row(b, q.id, cnt);
         }
         // the write pass's work lists: kept rows, and rows to traverse again
-        const int cls = cnt <= 4 ? 0 : (cnt <= 8 ? 1 : (cnt <= 16 ? 2 : 3));
+        const int cls = cnt <= 4 ? 0 : (cnt <= 8 ? 1 : (cnt <= 16 ? 2 : (cnt <= kRegRow ? 3 : 4)));
 #pragma unroll
-        for (int c = 0; c < 4; ++c) warp_append(b.kept[c], &b.list_cnt[4 + c], active && off >= 0 && cls == c, qp, lane);
+        for (int c = 0; c < 5; ++c) warp_append(b.kept[c], &b.list_cnt[4 + c], active && off >= 0 && cls == c, qp, lane);
         // rows to traverse again, by length (a warp then walks rows of similar length)
         const int rc = cnt <= 64 ? 0 : (cnt <= 128 ? 1 : (cnt <= 256 ? 2 : 3));
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            warp_append(b.relist[c], &b.list_cnt[8 + c], active && off < 0 && cnt > 0 && rc == c, qp, lane);
+            warp_append(b.relist[c], &b.list_cnt[9 + c], active && off < 0 && cnt > 0 && rc == c, qp, lane);
     }
     if (active) n_edge += cnt;
 }
@@ -356,6 +356,18 @@ __global__ void __launch_bounds__(32 * kCopyWarps) k_rim_copy(Plan p, QueryBufs 
     const int32_t nk = *((volatile int32_t *)&b.list_cnt[4 + cls]);
     const int32_t *kept = b.kept[cls];
     const int32_t nwarps = gridDim.x * kCopyWarps;
+    if (cls == 4) {  // kRegRow < d <= kKeepRow: one warp per row, copied as kept (the row sort orders it)
+        for (int32_t k = blockIdx.x * kCopyWarps + w; k < nk; k += nwarps) {
+            const int32_t qp = kept[k];
+            const int32_t stored = b.small_off[qp];
+            const int32_t id = b.pms[qp].id;
+            const int64_t base = row_off[id];
+            const int32_t deg = (int32_t)(row_off[id + 1] - base);
+            const int32_t off = BATCH ? b.plans[__ldg(b.graph_of + qp)].id_off : p.id_off;
+            for (int32_t i = lane; i < deg; i += 32) col_idx[base + i] = b.small[stored + i] - off;
+        }
+        return;
+    }
     for (int32_t k0 = (blockIdx.x * kCopyWarps + w) * 32; k0 < nk; k0 += nwarps * 32) {
         const int32_t k = k0 + lane;
         int32_t stored = 0, deg = 0, off = 0;
@@ -394,7 +406,7 @@ __global__ void __launch_bounds__(256) k_rim_relist(Plan p, QueryBufs b, const i
                                                     int32_t *__restrict__ col_idx)
 {
     const int cls = blockIdx.y;
-    const int32_t nr = *((volatile int32_t *)&b.list_cnt[8 + cls]);
+    const int32_t nr = *((volatile int32_t *)&b.list_cnt[9 + cls]);
     const int32_t *relist = b.relist[cls];
     unsigned n_cand = 0, n_re = 0, n_edge = 0;
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
@@ -711,7 +723,7 @@ static void rim_write_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only
                                int32_t *col_idx, cudaStream_t s)
 {
     const bool batch = b.plans != nullptr;
-    const dim3 cg(kRimWriteGrid / 4, 4);
+    const dim3 cg(kRimWriteGrid / 4, 5);
     if (batch) k_rim_copy<true><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
     else k_rim_copy<false><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
     if (fp64_only) {
