@@ -84,6 +84,7 @@ struct hrg_job {
     hrg_ctx *ctx = nullptr;
     Plan plan{};
     bool fp64 = false;
+    bool sampled = false;  // points drawn by the generator (else injected)
     bool open = false;
     bool finished = false;
     int32_t p_hub = 0;
@@ -416,6 +417,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     J.ctx = ctx;
     J.stream = st;
     J.fp64 = (flags & HRG_FLAG_FP64_ONLY) != 0 || R > 80.0;
+    J.sampled = sampled;
     J.row_off = row_off_out;
     Plan &p = J.plan;
     plan_bands(p, n, R, alpha, bands);
@@ -429,18 +431,36 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     if ((rc = ensure(ctx, hrg_ctx::W_PMS, sizeof(PMS) * n, &pms))) return rc;
     if (J.fp64 && (rc = ensure(ctx, hrg_ctx::W_PMS64, sizeof(PMS64) * n, &pms64))) return rc;
 
-    // 1. points.  A sampled graph's band layout is planned from the expected
-    // band counts (Eq. (1)); an injected point set's from its actual counts.
+    // 1. points and their (band, angular bucket).  A sampled graph's bucket
+    // layout is planned from the expected band counts (Eq. (1)) and filled by
+    // the sampler itself; an injected point set's from its actual counts.
     const double hub_cand = (prm && prm->hub_candidates > 0) ? (double)prm->hub_candidates : 512.0;
     int64_t cnt_copy[HRG_MAX_BANDS];
     int64_t *h_cnt = (int64_t *)ctx->pinned;
+    void *cnt = nullptr, *start = nullptr;
+    scanws = nullptr;
+    // bucket occupancy and start tables once the layout is known
+    auto bucket_tables = [&]() -> int {
+        plan_buckets(p, cnt_copy, &J.p_hub, hub_cand);
+        const size_t scan_bytes = std::max(scan_workspace_bytes(p.G), scan_workspace_bytes(n));
+        int e;
+        if ((e = ensure(ctx, hrg_ctx::W_CNT, sizeof(int32_t) * p.G, &cnt))) return e;
+        if ((e = ensure(ctx, hrg_ctx::W_START, sizeof(int32_t) * (p.G + 1), &start))) return e;
+        if ((e = ensure(ctx, hrg_ctx::W_SCAN, scan_bytes, &scanws))) return e;
+        return HRG_OK;
+    };
     CK(cudaEventRecord(ctx->ev[0], st));
     CK(cudaMemsetAsync(band_cnt, 0, sizeof(int64_t) * HRG_MAX_BANDS, st));
     if (sampled) {
-        CK(launch_sample(p, prm->seed, r_out, phi_out, st));
+        expected_band_counts(p, cnt_copy);
+        if ((rc = bucket_tables())) return rc;
+        CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * p.G, st));
+        CK(launch_sample_bucket(p, prm->seed, r_out, phi_out, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)cnt,
+                                (int64_t *)band_cnt, st));
         J.r = r_out;
         J.phi = phi_out;
-        expected_band_counts(p, cnt_copy);
+        CK(cudaEventRecord(ctx->ev[1], st));
+        CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));
     } else {
         CK(launch_count_bands(p, r_in, phi_in, (int64_t *)band_cnt, st));
         J.r = r_in;
@@ -448,20 +468,14 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
         CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
+        CK(cudaEventRecord(ctx->ev[1], st));
+        if ((rc = bucket_tables())) return rc;
+        CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * p.G, st));
+        CK(launch_bucket_hist(p, J.r, J.phi, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)cnt, st));
     }
-    CK(cudaEventRecord(ctx->ev[1], st));
-    plan_buckets(p, cnt_copy, &J.p_hub, hub_cand);
 
-    // 2. counting sort by (band, angular bucket); the exact band counts
-    void *cnt, *start;
-    const size_t scan_bytes = std::max(scan_workspace_bytes(p.G), scan_workspace_bytes(n));
-    if ((rc = ensure(ctx, hrg_ctx::W_CNT, sizeof(int32_t) * p.G, &cnt))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_START, sizeof(int32_t) * (p.G + 1), &start))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_bytes, &scanws))) return rc;
-    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * p.G, st));
-    CK(launch_bucket_hist(p, J.r, J.phi, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)cnt,
-                          sampled ? (int64_t *)band_cnt : nullptr, st));
-    if (sampled) CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));    CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, p.G, scanws, st));
+    // 2. counting sort by (band, angular bucket)
+    CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, p.G, scanws, st));
     CK(launch_scatter_soa(p, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, J.r, J.phi, (uint64_t *)A,
                           (PMS *)pms, (PMS64 *)pms64, st));
     CK(cudaEventRecord(ctx->ev[2], st));
@@ -659,15 +673,14 @@ extern "C" int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_p
     const Plan *P = (const Plan *)d_plans;
     CK(cudaEventRecord(ctx->ev[0], st));
     CK(launch_graph_of(P, count, (int32_t *)graph_of, st));
-    CK(launch_sample_batch(P, (int32_t *)graph_of, N, r_out, phi_out, st));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * G, st));
+    CK(launch_sample_bucket_batch(P, (int32_t *)graph_of, N, r_out, phi_out, (int32_t *)gbuf, (int32_t *)slot,
+                                  (int32_t *)cnt, st));
     J.r = r_out;
     J.phi = phi_out;
     CK(cudaEventRecord(ctx->ev[1], st));
 
     // 2. counting sort by (graph, band, angular bucket); hub query list
-    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * G, st));
-    CK(launch_bucket_hist_batch(P, (int32_t *)graph_of, N, r_out, phi_out, (int32_t *)gbuf, (int32_t *)slot,
-                                (int32_t *)cnt, st));
     CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, G, scanws, st));
     CK(launch_scatter_soa_batch(P, (int32_t *)graph_of, N, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, r_out,
                                 phi_out, (uint64_t *)A, (PMS *)pms, (PMS64 *)pms64, st));
@@ -767,22 +780,25 @@ extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
     out->big_rows = job->lists[2];
     out->mu = job->plan.mu;
     for (int k = 0; k < 8; ++k) out->stage_ms[k] = job->stage_ms[k];
-    // kernels launched: points (1), bucket histogram (1), bucket scan,
-    // structure-of-arrays scatter (1), count (hub 3, rim 1), row-offset scan,
-    // write (hub 3, rim 1), row sorts (warp 1, CTA 1, big 7)
+    // kernels launched: points with their buckets (1; an injected point set:
+    // band counts + bucket histogram, 2), bucket scan, structure-of-arrays
+    // scatter (1), count (hub 3, rim 1), row-offset scan, write (hub 3, rim
+    // 1), row sorts (warp 1, CTA 1, big 7)
     const int64_t n = job->plan.n;
+    const int scatter = 1;
     int L;
     if (job->batch) {
-        // graph map, points, bucket histogram, bucket scan, structure-of-arrays
+        // graph map, points with their buckets, bucket scan, structure-of-arrays
         // scatter, hub count + scan (+ fill), count, row-offset scan
-        L = 1 + 1 + 1 + scan_launches(job->batch_G) + 1 + 1 + scan_launches(job->batch) +
+        L = 1 + 1 + scan_launches(job->batch_G) + scatter + 1 + scan_launches(job->batch) +
             (job->p_hub > 0 ? 1 : 0) + (job->p_hub > 0 ? 3 : 0) + (job->qb.n_sectors > 0 ? 1 : 0) + scan_launches(n);
         if (job->finished) L += (job->p_hub > 0 ? 3 : 0) + (job->qb.n_sectors > 0 ? 1 : 0) + sort_launches(job->lists);
         out->launches = L;
         out->buckets = job->batch_G;
         return HRG_OK;
     }
-    L = 1 + 1 + scan_launches(job->plan.G) + 1 + query_launches(job->plan, job->p_hub, false) + scan_launches(n);
+    L = (job->sampled ? 1 : 2) + scan_launches(job->plan.G) + scatter + query_launches(job->plan, job->p_hub, false) +
+        scan_launches(n);
     if (job->finished) L += query_launches(job->plan, job->p_hub, true) + sort_launches(job->lists);
     out->launches = L;
     return HRG_OK;

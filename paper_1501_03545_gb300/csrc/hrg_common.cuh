@@ -99,14 +99,33 @@ __device__ __forceinline__ double log_table(double x, const double *tab)
     return fma((double)e, kLn2Hi, tab[128 + j]) + fma((double)e, kLn2Lo, l1p);
 }
 
+// acosh(x) for x >= 2^8 from the series
+//   acosh(x) = log(2x) + log((1 + sqrt(1 - s)) / 2)
+//            = log(2x) - s/4 - 3 s^2/32 - 5 s^3/96 - 35 s^4/1024 - ...,  s = 1/x^2.
+// With s <= 2^-16 the first dropped term is below 2^-68; for x >= 2^24 the
+// whole sum is below 2^-50 against log(2x) > 17 and is skipped.  s comes from
+// the float reciprocal of x refined by one Newton step (relative error
+// ~2^-46, i.e. ~2^-64 absolute in s/4).
+__device__ __forceinline__ double acosh_series(double x, const double *log_tab)
+{
+    double a = log_table(x + x, log_tab);
+    if (x < 0x1p24) {
+        const double y0 = (double)__frcp_rn((float)x);
+        const double y = fma(y0, fma(-x, y0, 1.0), y0);
+        const double s = y * y;
+        a -= s * fma(s, fma(s, 5.0 / 96.0, 3.0 / 32.0), 0.25);
+    }
+    return a;
+}
+
 // Radius of Eq. (1)'s inverse CDF, r = acosh(x) / alpha with x = 1 + u_r
-// (cosh(alpha R) - 1).  For x >= 2^24, acosh(x) = log(2x) - 1/(4x^2) - ...
-// and the dropped terms are below 2^-50 against log(2x) > 17: the log alone
-// is exact to well under an ulp there (and skips acosh's square root).
+// (cosh(alpha R) - 1).  Above x = 2^8 the series (no square root, and one
+// short branch where the library acosh would make a warp run both paths);
+// below, the library acosh.
 __device__ __forceinline__ double radius_of(double u_r, double big, double inv_alpha, const double *log_tab)
 {
     const double x = __dadd_rn(1.0, __dmul_rn(u_r, big));
-    const double a = x >= 0x1p24 ? log_table(x + x, log_tab) : acosh(x);
+    const double a = x >= 0x1p8 ? acosh_series(x, log_tab) : acosh(x);
     return a * inv_alpha;
 }
 

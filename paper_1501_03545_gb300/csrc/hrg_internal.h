@@ -10,15 +10,19 @@ namespace hrg {
 // The sampler's table of 1/F_j and log F_j (log_table); once per device.
 cudaError_t upload_log_table();
 // Sampler of Algorithm 1 (angle and radius draws, Eq. (1)): writes r, phi in
-// vertex-id order.
-cudaError_t launch_sample(const Plan &p, uint64_t seed, double *r, double *phi, cudaStream_t s);
+// vertex-id order, and with them every point's angular bucket (gbuf), its
+// rank inside the bucket (slot; order inside a bucket is unspecified), the
+// bucket occupancy (cnt, zeroed by the caller) and the exact per-band counts
+// (band_cnt, zeroed by the caller) under the plan's bucket layout.
+cudaError_t launch_sample_bucket(const Plan &p, uint64_t seed, double *r, double *phi, int32_t *gbuf, int32_t *slot,
+                                 int32_t *cnt, int64_t *band_cnt, cudaStream_t s);
 // Per-band point counts of an injected point set.
 cudaError_t launch_count_bands(const Plan &p, const double *r, const double *phi, int64_t *band_cnt, cudaStream_t s);
-// Angular-bucket id of every point (gbuf, id order), bucket occupancy (cnt)
-// and the point's rank inside its bucket (slot; order inside a bucket is
-// unspecified); with band_cnt non-null, also the exact per-band counts.
+// The same bucket data for an injected point set: angular-bucket id of every
+// point (gbuf, id order), bucket occupancy (cnt) and the point's rank inside
+// its bucket (slot).
 cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi, int32_t *gbuf, int32_t *slot,
-                               int32_t *cnt, int64_t *band_cnt, cudaStream_t s);
+                               int32_t *cnt, cudaStream_t s);
 // Structure-of-arrays in bucket order (point i at start[gbuf[i]] + slot[i]):
 // fixed-point angle, FP32 scaled exps + id; optionally the FP64 data of the
 // plain double-precision path.
@@ -29,10 +33,8 @@ cudaError_t launch_scatter_soa(const Plan &p, const int32_t *gbuf, const int32_t
 // Batches: plans[NG] in device memory, graph g owning positions and global
 // ids [plans[g].id_off, plans[g].id_off + plans[g].n).
 cudaError_t launch_graph_of(const Plan *plans, int NG, int32_t *graph_of, cudaStream_t s);
-cudaError_t launch_sample_batch(const Plan *plans, const int32_t *graph_of, int64_t N, double *r, double *phi,
-                                cudaStream_t s);
-cudaError_t launch_bucket_hist_batch(const Plan *plans, const int32_t *graph_of, int64_t N, const double *r,
-                                     const double *phi, int32_t *gbuf, int32_t *slot, int32_t *cnt, cudaStream_t s);
+cudaError_t launch_sample_bucket_batch(const Plan *plans, const int32_t *graph_of, int64_t N, double *r, double *phi,
+                                       int32_t *gbuf, int32_t *slot, int32_t *cnt, cudaStream_t s);
 cudaError_t launch_scatter_soa_batch(const Plan *plans, const int32_t *graph_of, int64_t N, const int32_t *gbuf,
                                      const int32_t *slot, const int32_t *start, const double *r, const double *phi,
                                      uint64_t *A, PMS *pms, PMS64 *pms64, cudaStream_t s);
@@ -52,6 +54,32 @@ constexpr int kRegRow = 32;       // rows up to this are sorted in registers by 
 constexpr int kKeepRow = 64;      // rows up to this are kept by the count pass (no second traversal)
 constexpr int kWarpRow = 1024;    // rows up to this: one warp, bucket sort in shared memory
 constexpr int kSmemRow = 12288;   // rows up to this: one CTA, bucket sort in shared memory
+
+// Up to 64 ids sorted ascending by a bitonic network over a warp's registers:
+// element i in lane i mod 32 (register a for i < 32, b for i >= 32), pads
+// 0x7fffffff.  Partners j < 32 apart are exchanged by shuffles, the pair 32
+// apart sits inside a lane; the lower index of a pair keeps the minimum when
+// its block sorts ascending.
+__device__ __forceinline__ void warp_bitonic64(int32_t &a, int32_t &b, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 32) {  // k = 64: every block ascending
+                const int32_t lo = min(a, b), hi = max(a, b);
+                a = lo;
+                b = hi;
+            } else {
+                const int32_t pa = __shfl_xor_sync(0xffffffffu, a, j), pb = __shfl_xor_sync(0xffffffffu, b, j);
+                const bool lower = (lane & j) == 0;
+                const bool up_a = (lane & k) == 0, up_b = ((lane + 32) & k) == 0;
+                a = (lower == up_a) ? min(a, pa) : max(a, pa);
+                b = (lower == up_b) ? min(b, pb) : max(b, pb);
+            }
+        }
+    }
+}
 
 struct QueryBufs {
     const uint64_t *A;        // [n] fixed-point angles, bucket order

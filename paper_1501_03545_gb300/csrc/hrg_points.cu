@@ -46,18 +46,35 @@ __device__ __forceinline__ void band_hist_flush(const Plan &p, int *sh, int64_t 
 // Algorithm 1's two draws: phi uniform on [0, 2pi) and r with density
 // Eq. (1), by the inverse CDF r = acosh(1 + u (cosh(alpha R) - 1)) / alpha.
 // Uniforms come from Philox4x32-10 at counter = vertex id, key = seed.
-__global__ void k_sample(Plan p, uint64_t seed, double *__restrict__ r_out, double *__restrict__ phi_out)
+// The bucket layout of a sampled graph is planned before the draws (from the
+// expected band counts), so the same pass files every point under its
+// (band, angular bucket): gbuf, the bucket occupancy cnt, the point's rank in
+// its bucket (slot) and the exact per-band counts.  The sampler is bound by
+// the FP64 pipe, the bucket atomics by memory latency: together they overlap.
+__global__ void k_sample_bucket(Plan p, uint64_t seed, double *__restrict__ r_out, double *__restrict__ phi_out,
+                                int32_t *__restrict__ gbuf, int32_t *__restrict__ slot, int32_t *__restrict__ cnt,
+                                int64_t *__restrict__ band_cnt)
 {
     __shared__ double s_tab[256];
+    __shared__ int sh[HRG_MAX_BANDS];
+    for (int k = threadIdx.x; k < HRG_MAX_BANDS; k += blockDim.x) sh[k] = 0;
     load_log_tab(s_tab);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
         const U4 w = philox_block((uint64_t)i, seed);
         const double u_phi = unit53(w.x, w.y);
         const double u_r = unit53(w.z, w.w);
-        phi_out[i] = __dmul_rn(u_phi, kTwoPi);
-        r_out[i] = radius_of(u_r, p.big, p.inv_alpha, s_tab);
+        const double ph = __dmul_rn(u_phi, kTwoPi);
+        const double rr = radius_of(u_r, p.big, p.inv_alpha, s_tab);
+        phi_out[i] = ph;
+        r_out[i] = rr;
+        const int band = band_of(p, rr);
+        const int64_t g = bucket_of(p, band, angle_key(ph));
+        gbuf[i] = (int32_t)g;
+        slot[i] = atomicAdd(&cnt[g], 1);
+        atomicAdd(&sh[band], 1);
     }
+    band_hist_flush(p, sh, band_cnt);
 }
 
 __global__ void k_count_bands(Plan p, const double *__restrict__ r, int64_t *__restrict__ band_cnt)
@@ -71,26 +88,19 @@ __global__ void k_count_bands(Plan p, const double *__restrict__ r, int64_t *__r
     band_hist_flush(p, sh, band_cnt);
 }
 
-// Bucket of every point (gbuf, id order), bucket occupancy, and the point's
-// rank inside its bucket (slot: the count it found there).
-// The exact per-band counts too (band_cnt, when the layout was planned from
-// their expectation).
+// Bucket of every point of an injected point set (gbuf, id order), bucket
+// occupancy, and the point's rank inside its bucket (slot: the count it found
+// there).
 __global__ void k_bucket_hist(Plan p, const double *__restrict__ r, const double *__restrict__ phi,
-                              int32_t *__restrict__ gbuf, int32_t *__restrict__ slot, int32_t *__restrict__ cnt,
-                              int64_t *__restrict__ band_cnt)
+                              int32_t *__restrict__ gbuf, int32_t *__restrict__ slot, int32_t *__restrict__ cnt)
 {
-    __shared__ int sh[HRG_MAX_BANDS];
-    for (int k = threadIdx.x; k < HRG_MAX_BANDS; k += blockDim.x) sh[k] = 0;
-    __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
         const int band = band_of(p, r[i]);
         const int64_t g = bucket_of(p, band, angle_key(phi[i]));
         gbuf[i] = (int32_t)g;
         slot[i] = atomicAdd(&cnt[g], 1);
-        if (band_cnt) atomicAdd(&sh[band], 1);
     }
-    if (band_cnt) band_hist_flush(p, sh, band_cnt);
 }
 
 // Structure of arrays in (band, bucket) order, written from id order: point i
@@ -130,8 +140,10 @@ __global__ void k_graph_of(const Plan *__restrict__ plans, int32_t *__restrict__
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) graph_of[off + i] = g;
 }
 
-__global__ void k_sample_batch(const Plan *__restrict__ plans, const int32_t *__restrict__ graph_of, int64_t N,
-                               double *__restrict__ r_out, double *__restrict__ phi_out)
+__global__ void k_sample_bucket_batch(const Plan *__restrict__ plans, const int32_t *__restrict__ graph_of,
+                                      int64_t N, double *__restrict__ r_out, double *__restrict__ phi_out,
+                                      int32_t *__restrict__ gbuf, int32_t *__restrict__ slot,
+                                      int32_t *__restrict__ cnt)
 {
     __shared__ double s_tab[256];
     load_log_tab(s_tab);
@@ -141,20 +153,11 @@ __global__ void k_sample_batch(const Plan *__restrict__ plans, const int32_t *__
         const U4 w = philox_block((uint64_t)(i - p.id_off), p.seed);
         const double u_phi = unit53(w.x, w.y);
         const double u_r = unit53(w.z, w.w);
-        phi_out[i] = __dmul_rn(u_phi, kTwoPi);
-        r_out[i] = radius_of(u_r, p.big, p.inv_alpha, s_tab);
-    }
-}
-
-__global__ void k_bucket_hist_batch(const Plan *__restrict__ plans, const int32_t *__restrict__ graph_of, int64_t N,
-                                    const double *__restrict__ r, const double *__restrict__ phi,
-                                    int32_t *__restrict__ gbuf, int32_t *__restrict__ slot, int32_t *__restrict__ cnt)
-{
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        const Plan &p = plans[__ldg(graph_of + i)];
-        const int band = band_of(p, r[i]);
-        const int64_t g = bucket_of(p, band, angle_key(phi[i]));
+        const double ph = __dmul_rn(u_phi, kTwoPi);
+        const double rr = radius_of(u_r, p.big, p.inv_alpha, s_tab);
+        phi_out[i] = ph;
+        r_out[i] = rr;
+        const int64_t g = bucket_of(p, band_of(p, rr), angle_key(ph));
         gbuf[i] = (int32_t)g;
         slot[i] = atomicAdd(&cnt[g], 1);
     }
@@ -321,9 +324,11 @@ cudaError_t scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t N, void *ws
     return scan_impl<int32_t, int64_t>(in, out, N, (int64_t *)ws, s);
 }
 
-cudaError_t launch_sample(const Plan &p, uint64_t seed, double *r, double *phi, cudaStream_t s)
+cudaError_t launch_sample_bucket(const Plan &p, uint64_t seed, double *r, double *phi, int32_t *gbuf, int32_t *slot,
+                                 int32_t *cnt, int64_t *band_cnt, cudaStream_t s)
 {
-    k_sample<<<std::min(grid_for(p.n, kThreads, 4), kSampleGrid), kThreads, 0, s>>>(p, seed, r, phi);
+    k_sample_bucket<<<std::min(grid_for(p.n, kThreads, 4), kSampleGrid), kThreads, 0, s>>>(p, seed, r, phi, gbuf, slot,
+                                                                                           cnt, band_cnt);
     return cudaGetLastError();
 }
 
@@ -334,9 +339,9 @@ cudaError_t launch_count_bands(const Plan &p, const double *r, const double *, i
 }
 
 cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi, int32_t *gbuf, int32_t *slot,
-                               int32_t *cnt, int64_t *band_cnt, cudaStream_t s)
+                               int32_t *cnt, cudaStream_t s)
 {
-    k_bucket_hist<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, r, phi, gbuf, slot, cnt, band_cnt);
+    k_bucket_hist<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, r, phi, gbuf, slot, cnt);
     return cudaGetLastError();
 }
 
@@ -364,17 +369,11 @@ cudaError_t launch_graph_of(const Plan *plans, int NG, int32_t *graph_of, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_sample_batch(const Plan *plans, const int32_t *graph_of, int64_t N, double *r, double *phi,
-                                cudaStream_t s)
+cudaError_t launch_sample_bucket_batch(const Plan *plans, const int32_t *graph_of, int64_t N, double *r, double *phi,
+                                       int32_t *gbuf, int32_t *slot, int32_t *cnt, cudaStream_t s)
 {
-    k_sample_batch<<<std::min(grid_for(N, kThreads, 4), kSampleGrid), kThreads, 0, s>>>(plans, graph_of, N, r, phi);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bucket_hist_batch(const Plan *plans, const int32_t *graph_of, int64_t N, const double *r,
-                                     const double *phi, int32_t *gbuf, int32_t *slot, int32_t *cnt, cudaStream_t s)
-{
-    k_bucket_hist_batch<<<grid_for(N, kThreads, 4), kThreads, 0, s>>>(plans, graph_of, N, r, phi, gbuf, slot, cnt);
+    k_sample_bucket_batch<<<std::min(grid_for(N, kThreads, 4), kSampleGrid), kThreads, 0, s>>>(plans, graph_of, N, r,
+                                                                                               phi, gbuf, slot, cnt);
     return cudaGetLastError();
 }
 

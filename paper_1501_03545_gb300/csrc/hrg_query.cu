@@ -239,7 +239,7 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
             }
             b.small_off[qp] = off;
             b.deg[q.id] = cnt;
-            classify_row(b, q.id, cnt);
+            if (off < 0) classify_row(b, q.id, cnt);  // kept rows are sorted by k_rim_copy
         }
         // the write pass's work lists: kept rows, and rows to traverse again
         const int cls = cnt <= 4 ? 0 : (cnt <= 8 ? 1 : (cnt <= 16 ? 2 : (cnt <= kRegRow ? 3 : 4)));
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(32 * kCopyWarps) k_rim_copy(Plan p, QueryBufs 
     const int32_t nk = *((volatile int32_t *)&b.list_cnt[4 + cls]);
     const int32_t *kept = b.kept[cls];
     const int32_t nwarps = gridDim.x * kCopyWarps;
-    if (cls == 4) {  // kRegRow < d <= kKeepRow: one warp per row, copied as kept (the row sort orders it)
+    if (cls == 4) {  // kRegRow < d <= kKeepRow: one warp per row, sorted in its registers
         for (int32_t k = blockIdx.x * kCopyWarps + w; k < nk; k += nwarps) {
             const int32_t qp = kept[k];
             const int32_t stored = b.small_off[qp];
@@ -364,7 +364,11 @@ __global__ void __launch_bounds__(32 * kCopyWarps) k_rim_copy(Plan p, QueryBufs 
             const int64_t base = row_off[id];
             const int32_t deg = (int32_t)(row_off[id + 1] - base);
             const int32_t off = BATCH ? b.plans[__ldg(b.graph_of + qp)].id_off : p.id_off;
-            for (int32_t i = lane; i < deg; i += 32) col_idx[base + i] = b.small[stored + i] - off;
+            int32_t x = lane < deg ? b.small[stored + lane] : 0x7fffffff;
+            int32_t y = lane + 32 < deg ? b.small[stored + lane + 32] : 0x7fffffff;
+            warp_bitonic64(x, y, lane);
+            if (lane < deg) col_idx[base + lane] = x - off;
+            if (lane + 32 < deg) col_idx[base + lane + 32] = y - off;
         }
         return;
     }

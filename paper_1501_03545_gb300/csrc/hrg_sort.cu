@@ -103,31 +103,12 @@ __device__ __forceinline__ uint32_t row_range(int64_t n, const int32_t *graph_of
     return (uint32_t)(__ldg(noff + g + 1) - __ldg(noff + g));
 }
 
-// Rows of up to 64 ids: a bitonic network over the warp's registers, element
-// i in lane i mod 32 (register a for i < 32, b for i >= 32); partners j < 32
-// apart are exchanged by shuffles, the pair 32 apart inside a lane.  The
-// lower index of a pair keeps the minimum when its block sorts ascending.
+// Rows of up to 64 ids: the bitonic network over the warp's registers.
 __device__ __forceinline__ void warp_sort64(int32_t *row, int d, int lane)
 {
     int32_t a = lane < d ? row[lane] : 0x7fffffff;
     int32_t b = lane + 32 < d ? row[lane + 32] : 0x7fffffff;
-#pragma unroll
-    for (int k = 2; k <= 64; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j == 32) {  // k = 64: every block ascending
-                const int32_t lo = min(a, b), hi = max(a, b);
-                a = lo;
-                b = hi;
-            } else {
-                const int32_t pa = __shfl_xor_sync(0xffffffffu, a, j), pb = __shfl_xor_sync(0xffffffffu, b, j);
-                const bool lower = (lane & j) == 0;
-                const bool up_a = (lane & k) == 0, up_b = ((lane + 32) & k) == 0;
-                a = (lower == up_a) ? min(a, pa) : max(a, pa);
-                b = (lower == up_b) ? min(b, pb) : max(b, pb);
-            }
-        }
-    }
+    warp_bitonic64(a, b, lane);
     if (lane < d) row[lane] = a;
     if (lane + 32 < d) row[lane + 32] = b;
 }
