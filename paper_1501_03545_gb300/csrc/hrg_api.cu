@@ -108,7 +108,7 @@ struct hrg_ctx {
     enum { W_BANDCNT, W_GBUF, W_CNT, W_START, W_SLOT, W_A, W_PMS, W_PMS64, W_DEG, W_STATS, W_LIST0, W_LIST1,
            W_LIST2, W_LISTCNT, W_BIGTOT, W_SCAN, W_TMP, W_BUCKET, W_OUT_R, W_OUT_PHI, W_OUT_OFF, W_OUT_COL,
            W_HEAVY, W_CURSOR, W_SMALL, W_SMALLOFF, W_SMALLCUR, W_PLANS, W_NOFF, W_SOFF, W_GRAPHOF, W_HUBCNT,
-           W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_KEPT0, W_KEPT1, W_KEPT2, W_KEPT3, W_KEPT4, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
+           W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_POSOF, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
            W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
@@ -319,9 +319,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 16, &listcnt))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_BIGTOT, sizeof(int64_t), &bigtot))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_workspace_bytes(n), &scanws))) return rc;
-    void *kept[5], *relist[4];
-    for (int k = 0; k < 5; ++k)
-        if ((rc = ensure(ctx, hrg_ctx::W_KEPT0 + k, sizeof(int32_t) * n, &kept[k]))) return rc;
+    void *relist[4];
     for (int k = 0; k < 4; ++k)
         if ((rc = ensure(ctx, hrg_ctx::W_RELIST0 + k, sizeof(int32_t) * n, &relist[k]))) return rc;
     const Plan &p = J.plan;
@@ -331,7 +329,6 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     b.stats = (unsigned long long *)stats;
     for (int k = 0; k < 3; ++k) b.rows[k] = (int32_t *)lists[k];
     b.list_cnt = (int32_t *)listcnt;
-    for (int k = 0; k < 5; ++k) b.kept[k] = (int32_t *)kept[k];
     for (int k = 0; k < 4; ++k) b.relist[k] = (int32_t *)relist[k];
     b.big_total = (int64_t *)bigtot;
     // heavy hub segments (long hub ranges cut into CTA chunks) and hub row cursors
@@ -366,6 +363,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
         CK(cudaMemsetAsync(bigtot, 0, sizeof(int64_t), st));
         CK(cudaMemsetAsync(deg, 0, sizeof(int32_t) * n, st));
         CK(cudaMemsetAsync(small_cur, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(small_off, 0xFF, sizeof(int32_t) * n, st));  // -1: no kept row (hub positions too)
         CK(launch_count_hub(p, b, J.fp64, J.p_hub, st));
         CK(cudaEventRecord(ctx->ev[3], st));
         CK(launch_count_rim(p, b, J.fp64, st));
@@ -422,9 +420,10 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     Plan &p = J.plan;
     plan_bands(p, n, R, alpha, bands);
 
-    void *band_cnt, *gbuf, *slot, *A, *pms, *pms64 = nullptr, *scanws;
+    void *band_cnt, *gbuf, *slot, *A, *pms, *pms64 = nullptr, *scanws, *pos_of;
     int rc;
     if ((rc = ensure(ctx, hrg_ctx::W_BANDCNT, sizeof(int64_t) * HRG_MAX_BANDS, &band_cnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_POSOF, sizeof(int32_t) * n, &pos_of))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_GBUF, sizeof(int32_t) * n, &gbuf))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SLOT, sizeof(int32_t) * n, &slot))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_A, sizeof(uint64_t) * n, &A))) return rc;
@@ -477,7 +476,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     // 2. counting sort by (band, angular bucket)
     CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, p.G, scanws, st));
     CK(launch_scatter_soa(p, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, J.r, J.phi, (uint64_t *)A,
-                          (PMS *)pms, (PMS64 *)pms64, st));
+                          (PMS *)pms, (PMS64 *)pms64, (int32_t *)pos_of, st));
     CK(cudaEventRecord(ctx->ev[2], st));
     // the exact band counts (read back behind the scan and the scatter): hub
     // queries and empty innermost bands
@@ -496,6 +495,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     b.pms = (PMS *)pms;
     b.pms64 = (PMS64 *)pms64;
     b.start = (int32_t *)start;
+    b.pos_of = (int32_t *)pos_of;
     return count_and_offsets(ctx, J, n, st, row_off_out, n_entries);
 }
 
@@ -646,13 +646,14 @@ extern "C" int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_p
     J.batch_G = G;
 
     // device tables
-    void *d_plans, *d_noff, *d_soff, *graph_of, *gbuf, *slot, *A, *pms, *pms64 = nullptr, *cnt, *start, *scanws;
+    void *d_plans, *d_noff, *d_soff, *graph_of, *gbuf, *slot, *A, *pms, *pms64 = nullptr, *cnt, *start, *scanws, *pos_of;
     void *hub_cnt, *hub_off, *hub_pos = nullptr;
     int rc;
     if ((rc = ensure(ctx, hrg_ctx::W_PLANS, sizeof(Plan) * count, &d_plans))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_NOFF, sizeof(int64_t) * (count + 1), &d_noff))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SOFF, sizeof(int64_t) * (count + 1), &d_soff))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_GRAPHOF, sizeof(int32_t) * N, &graph_of))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_POSOF, sizeof(int32_t) * N, &pos_of))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_GBUF, sizeof(int32_t) * N, &gbuf))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SLOT, sizeof(int32_t) * N, &slot))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_A, sizeof(uint64_t) * N, &A))) return rc;
@@ -683,7 +684,7 @@ extern "C" int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_p
     // 2. counting sort by (graph, band, angular bucket); hub query list
     CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, G, scanws, st));
     CK(launch_scatter_soa_batch(P, (int32_t *)graph_of, N, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, r_out,
-                                phi_out, (uint64_t *)A, (PMS *)pms, (PMS64 *)pms64, st));
+                                phi_out, (uint64_t *)A, (PMS *)pms, (PMS64 *)pms64, (int32_t *)pos_of, st));
     CK(launch_hub_list(P, count, (int32_t *)start, (int32_t *)hub_cnt, (int32_t *)hub_off, nullptr, scanws, st,
                        false));
     int32_t *hh = (int32_t *)ctx->pinned;
@@ -704,6 +705,7 @@ extern "C" int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_p
     b.pms = (PMS *)pms;
     b.pms64 = (PMS64 *)pms64;
     b.start = (int32_t *)start;
+    b.pos_of = (int32_t *)pos_of;
     b.plans = P;
     b.graph_of = (int32_t *)graph_of;
     b.sec_off = (int64_t *)d_soff;

@@ -25,10 +25,10 @@ cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi
                                int32_t *cnt, cudaStream_t s);
 // Structure-of-arrays in bucket order (point i at start[gbuf[i]] + slot[i]):
 // fixed-point angle, FP32 scaled exps + id; optionally the FP64 data of the
-// plain double-precision path.
+// plain double-precision path.  pos_of[i] receives point i's position.
 cudaError_t launch_scatter_soa(const Plan &p, const int32_t *gbuf, const int32_t *slot, const int32_t *start,
                                const double *r, const double *phi, uint64_t *A, PMS *pms, PMS64 *pms64,
-                               cudaStream_t s);
+                               int32_t *pos_of, cudaStream_t s);
 
 // Batches: plans[NG] in device memory, graph g owning positions and global
 // ids [plans[g].id_off, plans[g].id_off + plans[g].n).
@@ -37,7 +37,7 @@ cudaError_t launch_sample_bucket_batch(const Plan *plans, const int32_t *graph_o
                                        int32_t *gbuf, int32_t *slot, int32_t *cnt, cudaStream_t s);
 cudaError_t launch_scatter_soa_batch(const Plan *plans, const int32_t *graph_of, int64_t N, const int32_t *gbuf,
                                      const int32_t *slot, const int32_t *start, const double *r, const double *phi,
-                                     uint64_t *A, PMS *pms, PMS64 *pms64, cudaStream_t s);
+                                     uint64_t *A, PMS *pms, PMS64 *pms64, int32_t *pos_of, cudaStream_t s);
 // hub queries of every graph: fill=false counts them (hub_cnt[NG]) and scans
 // into hub_off[NG+1]; fill=true writes their positions into hub_pos
 cudaError_t launch_hub_list(const Plan *plans, int NG, const int32_t *start, int32_t *hub_cnt, int32_t *hub_off,
@@ -92,9 +92,8 @@ struct QueryBufs {
     unsigned long long *stats;  // [8] counters: candidates, rechecks, edges, ..., [7] error flag
     int32_t *rows[3];         // ids of rows to sort: (kRegRow, kWarpRow], (kWarpRow, kSmemRow], > kSmemRow
     int32_t *list_cnt;        // [16] lengths: [0..2] the three sort lists, [3] heavy segments,
-                              //     [4..8] kept rim rows by size class, [9..12] rim rows to traverse again
-    int32_t *kept[5];         // [n] each: positions of rim queries whose row the count pass kept, by
-                              //     size: 1..4, 5..8, 9..16, 17..kRegRow, kRegRow+1..kKeepRow entries
+                              //     [4..7] rim rows to traverse again
+    const int32_t *pos_of;    // [n] by vertex id: its position in the band structure
     int32_t *relist[4];       // [n] each: positions of rim queries the write pass traverses again, by
                               //     length: up to 64, 128, 256 entries, longer
     int64_t *big_total;       // [1] sum of degrees of the longest rows
@@ -105,7 +104,7 @@ struct QueryBufs {
     int32_t *seg_cnt;         // [heavy_cap] entries found in each heavy segment (count pass)
     int32_t *col_out;         // CSR neighbour ids being written (write pass only)
     int32_t *small;           // [small_cap] rim rows of up to kKeepRow entries kept by the count pass
-    int32_t *small_off;       // [n] by position: start of the kept row in small, -1 if not kept
+    int32_t *small_off;       // [n] by position: start of the kept row in small, -1 if none
     unsigned long long *small_cursor;  // [1] bump allocator over small
     int64_t small_cap;
     // batches of graphs (null / 0 for a single graph)

@@ -104,14 +104,15 @@ __global__ void k_bucket_hist(Plan p, const double *__restrict__ r, const double
 }
 
 // Structure of arrays in (band, bucket) order, written from id order: point i
-// goes to position start[gbuf[i]] + slot[i].
+// goes to position start[gbuf[i]] + slot[i], recorded in pos_of[i].
 __device__ __forceinline__ void place_point(const Plan &p, int64_t i, const int32_t *__restrict__ gbuf,
                                             const int32_t *__restrict__ slot, const int32_t *__restrict__ start,
                                             const double *__restrict__ r, const double *__restrict__ phi,
                                             uint64_t *__restrict__ A, PMS *__restrict__ pms,
-                                            PMS64 *__restrict__ pms64)
+                                            PMS64 *__restrict__ pms64, int32_t *__restrict__ pos_of)
 {
     const int64_t k = (int64_t)__ldg(start + gbuf[i]) + slot[i];
+    pos_of[i] = (int32_t)k;
     const double rr = r[i], ph = phi[i];
     A[k] = angle_key(ph);
     pms[k] = scaled_exps(p, rr, (int32_t)i);
@@ -121,11 +122,11 @@ __device__ __forceinline__ void place_point(const Plan &p, int64_t i, const int3
 __global__ void k_scatter_soa(Plan p, const int32_t *__restrict__ gbuf, const int32_t *__restrict__ slot,
                               const int32_t *__restrict__ start, const double *__restrict__ r,
                               const double *__restrict__ phi, uint64_t *__restrict__ A, PMS *__restrict__ pms,
-                              PMS64 *__restrict__ pms64)
+                              PMS64 *__restrict__ pms64, int32_t *__restrict__ pos_of)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride)
-        place_point(p, i, gbuf, slot, start, r, phi, A, pms, pms64);
+        place_point(p, i, gbuf, slot, start, r, phi, A, pms, pms64, pos_of);
 }
 
 // ---------------------------------------------------------------------------
@@ -167,11 +168,11 @@ __global__ void k_scatter_soa_batch(const Plan *__restrict__ plans, const int32_
                                     const int32_t *__restrict__ gbuf, const int32_t *__restrict__ slot,
                                     const int32_t *__restrict__ start, const double *__restrict__ r,
                                     const double *__restrict__ phi, uint64_t *__restrict__ A, PMS *__restrict__ pms,
-                                    PMS64 *__restrict__ pms64)
+                                    PMS64 *__restrict__ pms64, int32_t *__restrict__ pos_of)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
-        place_point(plans[__ldg(graph_of + i)], i, gbuf, slot, start, r, phi, A, pms, pms64);
+        place_point(plans[__ldg(graph_of + i)], i, gbuf, slot, start, r, phi, A, pms, pms64, pos_of);
 }
 
 // hub queries of graph g: its positions before its first rim-band bucket
@@ -346,9 +347,11 @@ cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi
 }
 
 cudaError_t launch_scatter_soa(const Plan &p, const int32_t *gbuf, const int32_t *slot, const int32_t *start,
-                               const double *r, const double *phi, uint64_t *A, PMS *pms, PMS64 *pms64, cudaStream_t s)
+                               const double *r, const double *phi, uint64_t *A, PMS *pms, PMS64 *pms64,
+                               int32_t *pos_of, cudaStream_t s)
 {
-    k_scatter_soa<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, gbuf, slot, start, r, phi, A, pms, pms64);
+    k_scatter_soa<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, gbuf, slot, start, r, phi, A, pms, pms64,
+                                                                   pos_of);
     return cudaGetLastError();
 }
 
@@ -379,10 +382,10 @@ cudaError_t launch_sample_bucket_batch(const Plan *plans, const int32_t *graph_o
 
 cudaError_t launch_scatter_soa_batch(const Plan *plans, const int32_t *graph_of, int64_t N, const int32_t *gbuf,
                                      const int32_t *slot, const int32_t *start, const double *r, const double *phi,
-                                     uint64_t *A, PMS *pms, PMS64 *pms64, cudaStream_t s)
+                                     uint64_t *A, PMS *pms, PMS64 *pms64, int32_t *pos_of, cudaStream_t s)
 {
     k_scatter_soa_batch<<<grid_for(N, kThreads, 4), kThreads, 0, s>>>(plans, graph_of, N, gbuf, slot, start, r, phi,
-                                                                       A, pms, pms64);
+                                                                       A, pms, pms64, pos_of);
     return cudaGetLastError();
 }
 

@@ -148,13 +148,12 @@ __device__ __forceinline__ void warp_append(int32_t *list, int32_t *count, bool 
 }
 
 // ---------------------------------------------------------------------------
-// ---------------------------------------------------------------------------
-// One query, one thread (rim bands).  Rows of up to kRegRow entries are kept
-// sorted in registers.  The count pass stores such a row in the row buffer
-// (b.small) and records where (b.small_off[position]); the write pass then
-// copies it instead of traversing the query again (k_rim_copy).  Longer
-// rows, and rows that did not fit in the buffer, are traversed again by the
-// write pass.
+// One query, one thread (rim bands).  The count pass stores a row of up to
+// kKeepRow entries in the row buffer (b.small) and records where
+// (b.small_off[position]); the write pass then sorts and copies it instead of
+// traversing the query again (k_rim_copy).  Longer rows, and rows that did
+// not fit in the buffer, are traversed again by the write pass, which keeps
+// rows of up to kRegRow entries sorted in registers.
 // ---------------------------------------------------------------------------
 // The traversal.  Count pass: every query of the sector; write pass: only
 // queries whose row was not kept (no warp-collective operations there, so
@@ -188,11 +187,22 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
             const Ranges rg = band_ranges(p, b.start, q, Aq, j);
             for (int part = 0; part < 2; ++part) {
                 const int32_t s = part ? rg.s1 : rg.s0, e = part ? rg.e1 : rg.e0;
+                // the next candidate's data is loaded one iteration ahead
+                uint64_t An = 0;
+                PMS cn{};
+                if (s < e) {
+                    An = __ldg(b.A + s);
+                    cn = b.pms[s];
+                }
                 for (int32_t c = s; c < e; ++c) {
+                    const uint64_t Ac = An;
+                    const PMS cc = cn;
+                    if (c + 1 < e) {
+                        An = __ldg(b.A + c + 1);
+                        cn = b.pms[c + 1];
+                    }
                     if (c == qp) continue;
-                    const uint64_t Ac = __ldg(b.A + c);
                     if (rg.W != kFullCircle && !within(Aq, Ac, rg.W)) continue;
-                    const PMS cc = b.pms[c];
                     if (!decide_loaded<F64>(p, b, q, q64, Aq, Ac, cc, c, kFullCircle, n_cand, n_re)) continue;
                     const int32_t id = cc.id;
                     if (WRITE) {
@@ -241,15 +251,12 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
             b.deg[q.id] = cnt;
             if (off < 0) classify_row(b, q.id, cnt);  // kept rows are sorted by k_rim_copy
         }
-        // the write pass's work lists: kept rows, and rows to traverse again
-        const int cls = cnt <= 4 ? 0 : (cnt <= 8 ? 1 : (cnt <= 16 ? 2 : (cnt <= kRegRow ? 3 : 4)));
-#pragma unroll
-        for (int c = 0; c < 5; ++c) warp_append(b.kept[c], &b.list_cnt[4 + c], active && off >= 0 && cls == c, qp, lane);
-        // rows to traverse again, by length (a warp then walks rows of similar length)
+        // the write pass's work list: rows to traverse again, by length (a
+        // warp then walks rows of similar length); kept rows are found by id
         const int rc = cnt <= 64 ? 0 : (cnt <= 128 ? 1 : (cnt <= 256 ? 2 : 3));
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            warp_append(b.relist[c], &b.list_cnt[9 + c], active && off < 0 && cnt > 0 && rc == c, qp, lane);
+            warp_append(b.relist[c], &b.list_cnt[4 + c], active && off < 0 && cnt > 0 && rc == c, qp, lane);
     }
     if (active) n_edge += cnt;
 }
@@ -328,18 +335,26 @@ __device__ __forceinline__ void rim_sector(const Plan &p, const QueryBufs &b, in
     add_stats(b.stats, n_cand, n_re, n_edge);
 }
 
-// Write pass of the rim rows.  Kept rows: a warp takes 32 of them of one size
-// class (blockIdx.y: up to 4, 8, 16 or 32 entries), loads them row by row
-// (coalesced) into a shared-memory tile, every lane sorts its own row in
-// registers with the class's network, and the warp stores them row by row.
+// Write pass of the rim rows kept by the count pass, in vertex-id order: warp
+// w takes the ids [32 t, 32 t + 32) for t = w, w + (all warps), ..., lane l
+// the id 32 t + l.  A row whose position has a kept row (small_off >= 0, at
+// most kKeepRow entries) is read from the row buffer, sorted and stored at
+// its row offset.  Consecutive rows thus fill col_idx front to back in whole
+// sectors; the scattered accesses are reads of the row buffer instead.  Rows
+// of up to kRegRow entries: every lane loads its own row into registers (all
+// loads of the warp in flight together), sorts it with the network that fits
+// the longest of them and leaves it in the warp's shared-memory tile, which
+// the warp stores row by row (coalesced).  Longer kept rows are sorted one at
+// a time across the warp's registers.
 constexpr int kCopyWarps = 8;
 
 template <int N>
-__device__ __forceinline__ void sort_tile_row(int32_t (*T)[kRegRow + 1], int lane, int32_t deg, int32_t off)
+__device__ __forceinline__ void sort_tile_row(int32_t (*T)[kRegRow + 1], const int32_t *__restrict__ src, int lane,
+                                              int32_t deg, int32_t off)
 {
     int32_t v[kRegRow];
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = j < deg ? T[lane][j] : 0x7fffffff;
+    for (int j = 0; j < N; ++j) v[j] = j < deg ? __ldg(src + j) : 0x7fffffff;
     bitonic_regs<N>(v);
 #pragma unroll
     for (int j = 0; j < N; ++j)
@@ -351,55 +366,52 @@ __global__ void __launch_bounds__(32 * kCopyWarps) k_rim_copy(Plan p, QueryBufs 
                                                               int32_t *__restrict__ col_idx)
 {
     __shared__ int32_t tile[kCopyWarps][kRegRow][kRegRow + 1];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, cls = blockIdx.y;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int32_t(*T)[kRegRow + 1] = tile[w];
-    const int32_t nk = *((volatile int32_t *)&b.list_cnt[4 + cls]);
-    const int32_t *kept = b.kept[cls];
-    const int32_t nwarps = gridDim.x * kCopyWarps;
-    if (cls == 4) {  // kRegRow < d <= kKeepRow: one warp per row, sorted in its registers
-        for (int32_t k = blockIdx.x * kCopyWarps + w; k < nk; k += nwarps) {
-            const int32_t qp = kept[k];
-            const int32_t stored = b.small_off[qp];
-            const int32_t id = b.pms[qp].id;
-            const int64_t base = row_off[id];
-            const int32_t deg = (int32_t)(row_off[id + 1] - base);
-            const int32_t off = BATCH ? b.plans[__ldg(b.graph_of + qp)].id_off : p.id_off;
-            int32_t x = lane < deg ? b.small[stored + lane] : 0x7fffffff;
-            int32_t y = lane + 32 < deg ? b.small[stored + lane + 32] : 0x7fffffff;
-            warp_bitonic64(x, y, lane);
-            if (lane < deg) col_idx[base + lane] = x - off;
-            if (lane + 32 < deg) col_idx[base + lane + 32] = y - off;
-        }
-        return;
-    }
-    for (int32_t k0 = (blockIdx.x * kCopyWarps + w) * 32; k0 < nk; k0 += nwarps * 32) {
-        const int32_t k = k0 + lane;
-        int32_t stored = 0, deg = 0, off = 0;
+    const int64_t n = p.n, groups = (n + 31) >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * kCopyWarps;
+    for (int64_t t = (int64_t)blockIdx.x * kCopyWarps + w; t < groups; t += nwarps) {
+        const int64_t id = (t << 5) + lane;
+        int32_t stored = -1, deg = 0, off = 0;
         int64_t base = 0;
-        if (k < nk) {
-            const int32_t qp = kept[k];
-            stored = b.small_off[qp];
-            const int32_t id = b.pms[qp].id;
-            base = row_off[id];
-            deg = (int32_t)(row_off[id + 1] - base);
-            off = BATCH ? b.plans[__ldg(b.graph_of + qp)].id_off : p.id_off;
+        if (id < n) {
+            stored = b.small_off[__ldg(b.pos_of + id)];
+            if (stored >= 0) {
+                base = row_off[id];
+                deg = (int32_t)(row_off[id + 1] - base);
+                off = BATCH ? b.plans[__ldg(b.graph_of + id)].id_off : p.id_off;
+            }
         }
-        for (int i = 0; i < 32; ++i) {
+        const int32_t dt = (stored >= 0 && deg <= kRegRow) ? deg : 0;  // rows of the tile
+        const int32_t dmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)dt);
+        if (dmax > 0) {
+            const int32_t *src = b.small + (dt > 0 ? stored : 0);
+            if (dmax <= 4) sort_tile_row<4>(T, src, lane, dt, off);
+            else if (dmax <= 8) sort_tile_row<8>(T, src, lane, dt, off);
+            else if (dmax <= 16) sort_tile_row<16>(T, src, lane, dt, off);
+            else sort_tile_row<32>(T, src, lane, dt, off);
+            __syncwarp();
+            for (int i = 0; i < 32; ++i) {
+                const int64_t bi = __shfl_sync(0xffffffffu, base, i);
+                const int32_t di = __shfl_sync(0xffffffffu, dt, i);
+                if (lane < di) col_idx[bi + lane] = T[i][lane];
+            }
+            __syncwarp();
+        }
+        // kept rows of kRegRow < d <= kKeepRow entries: one at a time
+        unsigned longer = __ballot_sync(0xffffffffu, stored >= 0 && deg > kRegRow);
+        while (longer) {
+            const int i = __ffs(longer) - 1;
+            longer &= longer - 1;
             const int32_t si = __shfl_sync(0xffffffffu, stored, i), di = __shfl_sync(0xffffffffu, deg, i);
-            if (lane < di) T[i][lane] = b.small[si + lane];
-        }
-        __syncwarp();
-        if (cls == 0) sort_tile_row<4>(T, lane, deg, off);
-        else if (cls == 1) sort_tile_row<8>(T, lane, deg, off);
-        else if (cls == 2) sort_tile_row<16>(T, lane, deg, off);
-        else sort_tile_row<32>(T, lane, deg, off);
-        __syncwarp();
-        for (int i = 0; i < 32; ++i) {
+            const int32_t oi = __shfl_sync(0xffffffffu, off, i);
             const int64_t bi = __shfl_sync(0xffffffffu, base, i);
-            const int32_t di = __shfl_sync(0xffffffffu, deg, i);
-            if (lane < di) col_idx[bi + lane] = T[i][lane];
+            int32_t x = lane < di ? b.small[si + lane] : 0x7fffffff;
+            int32_t y = lane + 32 < di ? b.small[si + lane + 32] : 0x7fffffff;
+            warp_bitonic64(x, y, lane);
+            if (lane < di) col_idx[bi + lane] = x - oi;
+            if (lane + 32 < di) col_idx[bi + lane + 32] = y - oi;
         }
-        __syncwarp();
     }
 }
 
@@ -410,7 +422,7 @@ __global__ void __launch_bounds__(256) k_rim_relist(Plan p, QueryBufs b, const i
                                                     int32_t *__restrict__ col_idx)
 {
     const int cls = blockIdx.y;
-    const int32_t nr = *((volatile int32_t *)&b.list_cnt[9 + cls]);
+    const int32_t nr = *((volatile int32_t *)&b.list_cnt[4 + cls]);
     const int32_t *relist = b.relist[cls];
     unsigned n_cand = 0, n_re = 0, n_edge = 0;
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
@@ -435,9 +447,10 @@ __device__ __forceinline__ int graph_search(const int64_t *__restrict__ off, int
 }
 
 // Count pass.  One graph: block x is sector x.  A batch: block x is global
-// sector x; the sector table gives its graph.
+// sector x; the sector table gives its graph.  Four CTAs per SM leave 64
+// registers a thread, room for the candidate prefetch without spilling.
 template <bool F64, bool BATCH>
-__global__ void __launch_bounds__(256, 5) k_rim_sector(Plan p, QueryBufs b)
+__global__ void __launch_bounds__(256, 4) k_rim_sector(Plan p, QueryBufs b)
 {
     if (BATCH) {
         const int g = graph_search(b.sec_off, b.NG, blockIdx.x);
@@ -727,7 +740,7 @@ static void rim_write_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only
                                int32_t *col_idx, cudaStream_t s)
 {
     const bool batch = b.plans != nullptr;
-    const dim3 cg(kRimWriteGrid / 4, 5);
+    const unsigned cg = kRimWriteGrid / 2;
     if (batch) k_rim_copy<true><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
     else k_rim_copy<false><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
     if (fp64_only) {
