@@ -225,6 +225,28 @@ def run_serving(H, device, seconds, slots):
                       "seed 10000 + index, numpy draw seed %d" % (W.SERVE_RATE, W.SERVE_DRAW_SEED)}
 
 
+def run_properties(H, ctx, stream, graphs):
+    """Sec. 4.1 properties on the device (hrg_graph_props: degree tail
+    exponent, triads, triangles, clustering) of freshly generated graphs,
+    each timed as the host wall time of the call (it returns with results).
+    graphs: (workload, seed, d_min, with_triangles)."""
+    import torch
+
+    out = {}
+    for w, seed, d_min, tri in graphs:
+        g = H.generate(ctx, w.n, w.alpha, w.kbar, seed, stream=stream)
+        H.graph_props(ctx, g["row_off"], g["col_idx"], d_min=d_min, triangles=tri, stream=stream)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p = H.graph_props(ctx, g["row_off"], g["col_idx"], d_min=d_min, triangles=tri, stream=stream)
+        ms = (time.perf_counter() - t0) * 1e3
+        del g
+        p["ms"] = ms
+        p["gamma_expected"] = 2 * w.alpha + 1
+        out[w.name] = p
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -262,6 +284,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=2)
     ap.add_argument("--oracle-n", type=int, default=ORACLE_SAMPLE_N)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-props", action="store_true", help="skip the graph properties (Sec. 4.1)")
     ap.add_argument("--n", type=int, default=0, help="profiling only: same alpha/kbar/seed at another n")
     args = ap.parse_args()
 
@@ -412,6 +435,12 @@ def main():
     if args.serve_seconds > 0 and rank == 0:
         serving = run_serving(H, local, args.serve_seconds, args.serve_slots)
 
+    # graph properties of Sec. 4.1 on the device: the 1e6-vertex workload (the
+    # size of the paper's property study) and the timed graph
+    props = None
+    if not args.no_props and rank == 0:
+        props = run_properties(H, ctx, stream, [(W.MEDIUM, W.MEDIUM.seed, 30, True), (w, seed, 48, True)])
+
     # roofline of the dominant kernel: the rim count pass (k_rim_sector), one
     # launch per graph, timed by the library's CUDA events around exactly that
     # launch on the job stream
@@ -447,7 +476,7 @@ def main():
                            "path": "fp32 filter + fp64 recheck", "entries_per_step": n_entries,
                            "undirected_edges_per_s": value / 2,
                            "l2": "no flush: every step writes and reads >8 GB, far above the 126 MB L2"},
-                "fp64_plain": fp64, "batched": batched, "serving": serving, "stage_ms": stage, "e2e": e2e, "roofline": roof, "clocks": clocks,
+                "fp64_plain": fp64, "batched": batched, "serving": serving, "properties": props, "stage_ms": stage, "e2e": e2e, "roofline": roof, "clocks": clocks,
                 "cpu_baseline": cpu, "gpu_launches": last.get("launches", 0) * args.steps,
                 "job": {k: last[k] for k in ("R", "candidates", "rechecks", "bands", "hub_bands", "buckets",
                                              "hub_queries", "mid_rows", "big_rows", "mu")}}

@@ -232,6 +232,60 @@ int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_host, double 
 int hrg_row_offsets_noalloc(const int32_t *deg, int64_t n, int64_t *row_off, void *stream);
 
 /*
+ * Graph properties of Sec. 4.1, computed on the device over a canonical CSR
+ * (rows ascending, both directions of every edge, no self-loops: the
+ * generator's output).  Sec. 4.1 studies the degree distribution (a power law
+ * with exponent gamma = 2 alpha + 1, Sec. 2.1) and the clustering
+ * coefficient, which it defines as the fraction of closed triangles among
+ * triads (paths of length two).
+ *   row_off  device int64[n+1]; the ids of vertex v's neighbours are
+ *            col_idx[row_off[v] .. row_off[v+1]) (row_off[0] need not be 0)
+ *   col_idx  device int32, ids in [0, n)            (read only; may be null
+ *            without HRG_PROPS_TRIANGLES)
+ *   d_min    >= 1: the tail used for gamma
+ *   flags    HRG_PROPS_TRIANGLES to count triangles (degree-ordered
+ *            orientation; workspace ~ 16 B per vertex + 4 B per edge)
+ *   stream   cudaStream_t (as void*); the call returns with *out filled
+ * gamma is the discrete maximum-likelihood approximation of Clauset,
+ * Shalizi and Newman (SIAM Review 51, 2009, Eq. 3.7):
+ * 1 + tail_count / tail_log_sum.  Undefined values are NaN (gamma without a
+ * tail, clustering without triads, both clusterings without
+ * HRG_PROPS_TRIANGLES, where triangles is -1).
+ * Errors: HRG_EINVAL (n outside [0, 2^31), d_min < 1, null pointer, unknown
+ * flag), HRG_ENOMEM, HRG_ECUDA.
+ */
+#define HRG_PROPS_TRIANGLES 0x1u
+
+typedef struct hrg_props {
+    int64_t n;                    /* vertices                                           */
+    int64_t entries;              /* directed CSR entries, 2m                          */
+    int64_t max_degree;
+    int64_t d_min;                /* tail threshold used for gamma                     */
+    int64_t tail_count;           /* vertices of degree >= d_min                       */
+    double tail_log_sum;          /* sum over them of ln(d / (d_min - 1/2))            */
+    double gamma;                 /* 1 + tail_count / tail_log_sum                     */
+    int64_t triads;               /* sum over v of d_v (d_v - 1) / 2                   */
+    int64_t triangles;            /* closed triangles, each counted once               */
+    double clustering;            /* 3 triangles / triads (Sec. 4.1)                   */
+    double avg_local_clustering;  /* mean over all v of t_v / (d_v (d_v - 1) / 2), t_v
+                                     the triangles at v; vertices of degree < 2 add 0  */
+} hrg_props;
+
+int hrg_graph_props(hrg_ctx *ctx, int64_t n, const int64_t *row_off, const int32_t *col_idx, int64_t d_min,
+                    uint32_t flags, void *stream, hrg_props *out);
+
+/*
+ * hrg_degree_histogram -- hist[d] = vertices of degree d, d = 0..max_degree,
+ * of the CSR given by row_off (as for hrg_graph_props).
+ *   hist     device int64[max_degree + 1] (caller owned, overwritten)
+ * The call returns when hist is complete.
+ * Errors: HRG_EINVAL (a degree above max_degree -- hist then holds the
+ * others --, null pointer, n outside [0, 2^31), max_degree < 0), HRG_ECUDA.
+ */
+int hrg_degree_histogram(hrg_ctx *ctx, int64_t n, const int64_t *row_off, int64_t max_degree, int64_t *hist,
+                         void *stream);
+
+/*
  * Request server -- generation requests of different sizes and parameters on
  * one GPU with continuous batching.  The paper has no serving layer; this is
  * the request loop around Algorithm 1 for callers that submit many graphs.

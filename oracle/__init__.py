@@ -18,6 +18,12 @@ Functions and the passage each follows (von Looz, Meyerhenke, Prutkin, Staudt,
 * ``brute_csr``         -- the plain definition: all pairs, edge iff dist < R.
 * ``band_csr`` / ``band_rows`` -- an independent band algorithm for large n.
 * ``ties``              -- pairs within 1e-12 relative of the threshold.
+* ``graph_props``       -- Sec. 4.1 properties of a CSR: the degree tail's
+                           power-law exponent (discrete MLE approximation of
+                           Clauset, Shalizi and Newman, Eq. 3.7), triads,
+                           triangles, and the clustering coefficient as the
+                           fraction of closed triads; the mean local
+                           coefficient beside it.
 
 Every function here is pinned by ``tests/test_oracle*.py`` to something other
 than itself (an independent Philox, mpmath, scipy quadrature, the paper's
@@ -89,6 +95,9 @@ def lib():
             L.orc_bands_rows.argtypes = [_P, _P, _P, _I64, _P, _P, _P, _P]
             L.orc_bands_ties.argtypes = [_P, _P, _P, _D, _I64, _P]
             L.orc_bands_ties.restype = _I64
+            L.orc_degree_stats.argtypes = [_I64, _P, _I64, _P, _P]
+            L.orc_triangles.argtypes = [_I64, _P, _P, _P]
+            L.orc_triangles.restype = _I64
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_set_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -269,3 +278,38 @@ def generate(n: int, alpha: float, kbar: float, seed: int, method: str = "auto",
         method = "brute" if n <= 20000 else "bands"
     off, col = brute_csr(r, phi, R) if method == "brute" else band_csr(r, phi, R)
     return {"R": R, "r": r, "phi": phi, "row_off": off, "col_idx": col}
+
+
+def graph_props(row_off, col_idx, d_min: int, triangles: bool = True) -> dict:
+    """Sec. 4.1 properties of a canonical CSR (rows ascending, both directions).
+
+    gamma = 1 + tail_count / tail_log_sum over the vertices of degree >=
+    d_min (NaN for an empty tail); clustering = 3 triangles / triads (NaN
+    without triads); avg_local_clustering = the mean over all vertices of
+    t_v / (d_v (d_v - 1) / 2), vertices of degree < 2 counting 0."""
+    off = np.ascontiguousarray(np.asarray(row_off, dtype=np.int64))
+    col = np.ascontiguousarray(np.asarray(col_idx, dtype=np.int32))
+    n = len(off) - 1
+    oi = np.zeros(4, dtype=np.int64)
+    od = np.zeros(1, dtype=np.float64)
+    lib().orc_degree_stats(n, _ptr(off), int(d_min), _ptr(oi), _ptr(od))
+    res = {"n": n, "entries": int(oi[0]), "max_degree": int(oi[1]), "d_min": int(d_min),
+           "tail_count": int(oi[2]), "tail_log_sum": float(od[0]), "triads": int(oi[3])}
+    res["gamma"] = 1.0 + res["tail_count"] / res["tail_log_sum"] if res["tail_count"] > 0 else float("nan")
+    res["triangles"] = -1
+    res["clustering"] = float("nan")
+    res["avg_local_clustering"] = float("nan")
+    if triangles:
+        t = np.zeros(max(n, 1), dtype=np.int64)
+        colp = col if len(col) else np.zeros(1, dtype=np.int32)
+        T = int(lib().orc_triangles(n, _ptr(off), _ptr(colp), _ptr(t)))
+        t = t[:n]
+        res["triangles"] = T
+        res["triangles_per_vertex"] = t
+        if res["triads"] > 0:
+            res["clustering"] = 3.0 * T / res["triads"]
+        d = np.diff(off)
+        pairs = d * (d - 1) // 2
+        local = np.where(pairs > 0, t / np.maximum(pairs, 1), 0.0)
+        res["avg_local_clustering"] = float(local.sum() / n) if n > 0 else float("nan")
+    return res

@@ -502,3 +502,70 @@ void orc_set_threads(int t)
     (void)t;
 #endif
 }
+
+/* ---------------------------------------------------------------------------
+ * Graph properties of Sec. 4.1 over a canonical CSR (rows ascending, both
+ * directions of every edge).
+ *   - Degree tail: the power-law exponent by the discrete maximum-likelihood
+ *     approximation of Clauset, Shalizi and Newman (SIAM Review 51, 2009,
+ *     Eq. 3.7): gamma = 1 + N / sum ln(d / (d_min - 1/2)) over the N
+ *     vertices of degree d >= d_min.  Returned as its two sums.
+ *   - Triads: paths of length two, sum over v of d_v (d_v - 1) / 2.
+ *   - Triangles: vertex triples u < v < w with all three edges, each counted
+ *     once, found by walking N(u) and N(v) together above v; per-vertex
+ *     counts (each triangle at its three corners) for local clustering.
+ * The clustering coefficient of Sec. 4.1 is the fraction of closed triads:
+ * 3 triangles / triads.
+ * ------------------------------------------------------------------------- */
+void orc_degree_stats(int64_t n, const int64_t *row_off, int64_t d_min, int64_t *out_i, double *out_d)
+{
+    int64_t max_d = 0, tail = 0, triads = 0;
+    double logs = 0.0;
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t d = row_off[v + 1] - row_off[v];
+        if (d > max_d) max_d = d;
+        triads += d * (d - 1) / 2;
+        if (d >= d_min) {
+            ++tail;
+            logs += log((double)d / ((double)d_min - 0.5));
+        }
+    }
+    out_i[0] = row_off[n] - row_off[0];
+    out_i[1] = max_d;
+    out_i[2] = tail;
+    out_i[3] = triads;
+    out_d[0] = logs;
+}
+
+int64_t orc_triangles(int64_t n, const int64_t *row_off, const int32_t *col_idx, int64_t *t)
+{
+    int64_t total = 0;
+    if (t)
+        for (int64_t v = 0; v < n; ++v) t[v] = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        const int64_t ub = row_off[u], ue = row_off[u + 1];
+        for (int64_t a = ub; a < ue; ++a) {
+            const int32_t v = col_idx[a];
+            if (v <= u) continue;
+            /* common neighbours w > v: N(u) after v, N(v) from its first entry above v */
+            int64_t i = a + 1, j = row_off[v];
+            const int64_t je = row_off[v + 1];
+            while (j < je && col_idx[j] <= v) ++j;
+            while (i < ue && j < je) {
+                if (col_idx[i] < col_idx[j]) ++i;
+                else if (col_idx[i] > col_idx[j]) ++j;
+                else {
+                    ++total;
+                    if (t) {
+                        ++t[u];
+                        ++t[v];
+                        ++t[col_idx[i]];
+                    }
+                    ++i;
+                    ++j;
+                }
+            }
+        }
+    }
+    return total;
+}

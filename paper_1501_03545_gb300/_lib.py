@@ -22,8 +22,9 @@ EXPORTS = (
     "hrg_generate_from_points_begin", "hrg_generate_finish", "hrg_job_stats", "hrg_job_release",
     "hrg_generate", "hrg_generate_host", "hrg_last_error", "hrg_version", "hrg_row_offsets_noalloc",
     "hrg_generate_batch_begin", "hrg_server_create", "hrg_server_submit", "hrg_server_wait", "hrg_server_release",
-    "hrg_server_stats", "hrg_server_last_error", "hrg_server_destroy",
+    "hrg_server_stats", "hrg_server_last_error", "hrg_server_destroy", "hrg_graph_props", "hrg_degree_histogram",
 )
+HRG_PROPS_TRIANGLES = 0x1
 
 
 class HrgError(RuntimeError):
@@ -51,6 +52,16 @@ class hrg_stats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "stage_ms")}
         d["stage_ms"] = {s: float(self.stage_ms[i]) for i, s in enumerate(self.STAGES)}
         return d
+
+
+class hrg_props(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("entries", ctypes.c_int64), ("max_degree", ctypes.c_int64),
+                ("d_min", ctypes.c_int64), ("tail_count", ctypes.c_int64), ("tail_log_sum", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("triads", ctypes.c_int64), ("triangles", ctypes.c_int64),
+                ("clustering", ctypes.c_double), ("avg_local_clustering", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lock = threading.Lock()
@@ -105,6 +116,8 @@ def load(build_if_missing: bool = True):
         L.hrg_server_last_error.argtypes = [_P]
         L.hrg_server_last_error.restype = ctypes.c_char_p
         L.hrg_server_destroy.argtypes = [_P]
+        L.hrg_graph_props.argtypes = [_P, _I64, _P, _P, _I64, ctypes.c_uint32, _P, ctypes.POINTER(hrg_props)]
+        L.hrg_degree_histogram.argtypes = [_P, _I64, _P, _I64, _P, _P]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         _lib = L
@@ -204,6 +217,35 @@ def generate(ctx: Context, n, alpha, avg_degree, seed, R_override=0.0, fp64_only
     finally:
         L.hrg_job_release(job)
     return {"r": r, "phi": phi, "row_off": off, "col_idx": col[: ne.value], "stats": s.as_dict()}
+
+
+def graph_props(ctx: Context, row_off, col_idx=None, d_min=1, triangles=True, stream=None) -> dict:
+    """hrg_graph_props on a device CSR (torch tensors: row_off int64[n+1],
+    col_idx int32): degree tail exponent, triads, triangles, clustering."""
+    import torch
+
+    L = load()
+    dev = torch.device("cuda", ctx.device)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    n = row_off.numel() - 1
+    out = hrg_props()
+    col = _P(_dptr(col_idx)) if col_idx is not None and col_idx.numel() > 0 else _P(None)
+    ctx.check(L.hrg_graph_props(ctx.h, n, _P(_dptr(row_off)), col, int(d_min),
+                                HRG_PROPS_TRIANGLES if triangles else 0, _P(st.cuda_stream), ctypes.byref(out)))
+    return out.as_dict()
+
+
+def degree_histogram(ctx: Context, row_off, max_degree: int, stream=None):
+    """hrg_degree_histogram: int64 tensor hist[max_degree + 1] on the device."""
+    import torch
+
+    L = load()
+    dev = torch.device("cuda", ctx.device)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    hist = torch.empty(max_degree + 1, dtype=torch.int64, device=dev)
+    ctx.check(L.hrg_degree_histogram(ctx.h, row_off.numel() - 1, _P(_dptr(row_off)), int(max_degree),
+                                     _P(_dptr(hist)), _P(st.cuda_stream)))
+    return hist
 
 
 class BatchItems:

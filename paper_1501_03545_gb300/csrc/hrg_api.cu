@@ -109,6 +109,7 @@ struct hrg_ctx {
            W_LIST2, W_LISTCNT, W_BIGTOT, W_SCAN, W_TMP, W_BUCKET, W_OUT_R, W_OUT_PHI, W_OUT_OFF, W_OUT_COL,
            W_HEAVY, W_CURSOR, W_SMALL, W_SMALLOFF, W_SMALLCUR, W_PLANS, W_NOFF, W_SOFF, W_GRAPHOF, W_HUBCNT,
            W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_POSOF, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
+           W_PACC, W_POUTDEG, W_POUTOFF, W_POUTCOL, W_PTRI, W_PSCAN,
            W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
@@ -883,5 +884,103 @@ extern "C" int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_ho
     if (ne > 0) CK(cudaMemcpyAsync(col_idx_host, dcol, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaStreamSynchronize(cp));
+    return HRG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Graph properties of Sec. 4.1 (kernels in hrg_props.cu).
+// ---------------------------------------------------------------------------
+extern "C" int hrg_graph_props(hrg_ctx *ctx, int64_t n, const int64_t *row_off, const int32_t *col_idx,
+                               int64_t d_min, uint32_t flags, void *stream, hrg_props *out)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (!out) return set_err(ctx, HRG_EINVAL, "null out");
+    if (n < 0 || n > 0x7fffffffLL) return set_err(ctx, HRG_EINVAL, "n must be in [0, 2^31)");
+    if (n > 0 && !row_off) return set_err(ctx, HRG_EINVAL, "null row_off");
+    if (d_min < 1) return set_err(ctx, HRG_EINVAL, "d_min must be at least 1");
+    if (flags & ~HRG_PROPS_TRIANGLES) return set_err(ctx, HRG_EINVAL, "unknown flags");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    memset(out, 0, sizeof *out);
+    out->n = n;
+    out->d_min = d_min;
+    out->triangles = -1;
+    out->gamma = out->clustering = out->avg_local_clustering = std::nan("");
+    if (n == 0) return HRG_OK;
+    int rc;
+    void *acc;
+    if ((rc = ensure(ctx, hrg_ctx::W_PACC, 64, &acc))) return rc;
+    unsigned long long *ai = (unsigned long long *)acc;  // [0] max degree [1] tail [2] triads [3] triangles
+    double *ad = (double *)((char *)acc + 32);           // [0] tail log sum [1] local clustering sum
+    CK(cudaMemsetAsync(acc, 0, 64, st));
+    CK(launch_degree_stats(n, row_off, d_min, ai, ad, st));
+    char *hp = (char *)ctx->pinned;
+    CK(cudaMemcpyAsync(hp, acc, 64, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 64, row_off, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 72, row_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    unsigned long long hi[4];
+    double hd[2];
+    int64_t o0, on;
+    memcpy(hi, hp, 32);
+    memcpy(hd, hp + 32, 16);
+    memcpy(&o0, hp + 64, 8);
+    memcpy(&on, hp + 72, 8);
+    out->entries = on - o0;
+    out->max_degree = (int64_t)hi[0];
+    out->tail_count = (int64_t)hi[1];
+    out->triads = (int64_t)hi[2];
+    out->tail_log_sum = hd[0];
+    if (out->tail_count > 0) out->gamma = 1.0 + (double)out->tail_count / out->tail_log_sum;
+    if (!(flags & HRG_PROPS_TRIANGLES)) return HRG_OK;
+    if (out->entries > 0 && !col_idx) return set_err(ctx, HRG_EINVAL, "null col_idx");
+
+    // the neighbours ranked above each vertex, then the triangles
+    void *odeg, *ooff, *ocol, *tri, *scanws;
+    if ((rc = ensure(ctx, hrg_ctx::W_POUTDEG, sizeof(int32_t) * n, &odeg))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_POUTOFF, sizeof(int64_t) * (n + 1), &ooff))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_PTRI, sizeof(unsigned long long) * n, &tri))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_PSCAN, scan_workspace_bytes(n), &scanws))) return rc;
+    CK(launch_out_edges(n, row_off, col_idx, (int32_t *)odeg, nullptr, nullptr, false, st));
+    CK(scan_i32_to_i64((const int32_t *)odeg, (int64_t *)ooff, n, scanws, st));
+    CK(cudaMemcpyAsync(hp + 80, (int64_t *)ooff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int64_t m_up;
+    memcpy(&m_up, hp + 80, 8);
+    if ((rc = ensure(ctx, hrg_ctx::W_POUTCOL, sizeof(int32_t) * (m_up > 0 ? m_up : 1), &ocol))) return rc;
+    CK(cudaMemsetAsync(tri, 0, sizeof(unsigned long long) * n, st));
+    CK(launch_out_edges(n, row_off, col_idx, nullptr, (const int64_t *)ooff, (int32_t *)ocol, true, st));
+    CK(launch_triangles(n, (const int64_t *)ooff, (const int32_t *)ocol, (unsigned long long *)tri, ai + 3, st));
+    CK(launch_local_clustering(n, row_off, (const unsigned long long *)tri, ad + 1, st));
+    CK(cudaMemcpyAsync(hp, acc, 64, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    memcpy(hi, hp, 32);
+    memcpy(hd, hp + 32, 16);
+    out->triangles = (int64_t)hi[3];
+    if (out->triads > 0) out->clustering = 3.0 * (double)out->triangles / (double)out->triads;
+    out->avg_local_clustering = hd[1] / (double)n;
+    return HRG_OK;
+}
+
+extern "C" int hrg_degree_histogram(hrg_ctx *ctx, int64_t n, const int64_t *row_off, int64_t max_degree,
+                                    int64_t *hist, void *stream)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (n < 0 || n > 0x7fffffffLL) return set_err(ctx, HRG_EINVAL, "n must be in [0, 2^31)");
+    if ((n > 0 && !row_off) || !hist) return set_err(ctx, HRG_EINVAL, "null argument");
+    if (max_degree < 0) return set_err(ctx, HRG_EINVAL, "max_degree must be >= 0");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    void *acc;
+    if ((rc = ensure(ctx, hrg_ctx::W_PACC, 64, &acc))) return rc;
+    CK(cudaMemsetAsync(hist, 0, sizeof(int64_t) * (max_degree + 1), st));
+    CK(cudaMemsetAsync(acc, 0, sizeof(int), st));
+    if (n > 0)
+        CK(launch_degree_hist(n, row_off, max_degree, (unsigned long long *)hist, (int *)acc, st));
+    int *hflag = (int *)ctx->pinned;
+    CK(cudaMemcpyAsync(hflag, acc, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*hflag) return set_err(ctx, HRG_EINVAL, "a degree exceeds max_degree = %lld", (long long)max_degree);
     return HRG_OK;
 }
