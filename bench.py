@@ -227,22 +227,36 @@ def run_serving(H, device, seconds, slots):
 
 def run_properties(H, ctx, stream, graphs):
     """Sec. 4.1 properties on the device (hrg_graph_props: degree tail
-    exponent, triads, triangles, clustering) of freshly generated graphs,
-    each timed as the host wall time of the call (it returns with results).
-    graphs: (workload, seed, d_min, with_triangles)."""
+    exponent, triads, triangles, clustering) of freshly generated graphs, and
+    Sec. 4.2's random long-range edges (hrg_add_random_edges, 0.5 % of m),
+    each timed as the host wall time of the call (after one warm-up call up
+    to n = 1e7; the calls return with their results).  graphs: (workload,
+    seed, d_min, properties of the graph with the long-range edges too)."""
     import torch
 
-    out = {}
-    for w, seed, d_min, tri in graphs:
-        g = H.generate(ctx, w.n, w.alpha, w.kbar, seed, stream=stream)
-        H.graph_props(ctx, g["row_off"], g["col_idx"], d_min=d_min, triangles=tri, stream=stream)  # warm-up
+    def timed(f, warm):
+        if warm:
+            f()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        p = H.graph_props(ctx, g["row_off"], g["col_idx"], d_min=d_min, triangles=tri, stream=stream)
-        ms = (time.perf_counter() - t0) * 1e3
-        del g
+        r = f()
+        return r, (time.perf_counter() - t0) * 1e3
+
+    out = {}
+    for w, seed, d_min, lr_props in graphs:
+        g = H.generate(ctx, w.n, w.alpha, w.kbar, seed, stream=stream)
+        warm = w.n <= 10_000_000
+        p, ms = timed(lambda: H.graph_props(ctx, g["row_off"], g["col_idx"], d_min=d_min, stream=stream), warm)
         p["ms"] = ms
         p["gamma_expected"] = 2 * w.alpha + 1
+        count = -(-p["entries"] // 400)  # ceil(0.005 m), m = entries / 2
+        lr, lms = timed(lambda: H.add_random_edges(ctx, g["row_off"], g["col_idx"], count, 99, stream=stream), True)
+        del g
+        p["long_range"] = {"pairs": count, "added": lr["added"], "ms": lms}
+        if lr_props:
+            q = H.graph_props(ctx, lr["row_off"], lr["col_idx"], d_min=d_min, stream=stream)
+            p["long_range"].update({k: q[k] for k in ("gamma", "triangles", "clustering", "avg_local_clustering")})
+        del lr
         out[w.name] = p
     return out
 
@@ -435,11 +449,12 @@ def main():
     if args.serve_seconds > 0 and rank == 0:
         serving = run_serving(H, local, args.serve_seconds, args.serve_slots)
 
-    # graph properties of Sec. 4.1 on the device: the 1e6-vertex workload (the
-    # size of the paper's property study) and the timed graph
+    # graph properties of Sec. 4.1 and the random long-range edges of Sec. 4.2
+    # on the device: the 1e6-vertex workload (the size of the paper's property
+    # study) and the timed graph
     props = None
     if not args.no_props and rank == 0:
-        props = run_properties(H, ctx, stream, [(W.MEDIUM, W.MEDIUM.seed, 30, True), (w, seed, 48, True)])
+        props = run_properties(H, ctx, stream, [(W.MEDIUM, W.MEDIUM.seed, 30, True), (w, seed, 48, False)])
 
     # roofline of the dominant kernel: the rim count pass (k_rim_sector), one
     # launch per graph, timed by the library's CUDA events around exactly that

@@ -286,6 +286,31 @@ int hrg_degree_histogram(hrg_ctx *ctx, int64_t n, const int64_t *row_off, int64_
                          void *stream);
 
 /*
+ * hrg_add_random_edges -- the graph with random long-range edges (Sec. 4.2
+ * and its appendix: adding 0.5 % of the edges at random shortens the
+ * diameter while the other properties stay close).  Pair k = 0..count-1 draws
+ * the Philox4x32-10 block at counter 2^63 + k (words (k_lo, k_hi + 2^31, 0,
+ * 0); the point draws use counters below 2^31), key (seed_lo, seed_hi), and
+ * takes the vertices u = floor(w0 n / 2^64), v = floor(w1 n / 2^64) of its
+ * two 64-bit halves w0 = (x0 << 32) | x1, w1 = (x2 << 32) | x3.  Self-pairs,
+ * pairs drawn twice and pairs already present are dropped; the rest become
+ * undirected edges.  The paper's 0.5 % is count = ceil(0.005 m).
+ *   row_off, col_idx   device, the input CSR as for hrg_graph_props (read)
+ *   row_off_out        device int64[n+1] (caller owned): the new offsets, from 0
+ *   col_idx_out        device int32[col_capacity] (caller owned); 2m + 2 count
+ *                      always suffices
+ *   *entries_out       the new 2m; *added_out (may be null) the added edges
+ *   stream             cudaStream_t (as void*); the call returns when done
+ * The output is again canonical: rows ascending, symmetric, no self-loops.
+ * Errors: HRG_EINVAL (n outside [0, 2^31), count outside [0, 2^30], null
+ * pointer), HRG_EOVERFLOW (*entries_out above col_capacity: row_off_out is
+ * written, col_idx_out untouched), HRG_ENOMEM, HRG_ECUDA.
+ */
+int hrg_add_random_edges(hrg_ctx *ctx, int64_t n, const int64_t *row_off, const int32_t *col_idx, int64_t count,
+                         uint64_t seed, void *stream, int64_t *row_off_out, int32_t *col_idx_out,
+                         int64_t col_capacity, int64_t *entries_out, int64_t *added_out);
+
+/*
  * Request server -- generation requests of different sizes and parameters on
  * one GPU with continuous batching.  The paper has no serving layer; this is
  * the request loop around Algorithm 1 for callers that submit many graphs.

@@ -24,6 +24,9 @@ Functions and the passage each follows (von Looz, Meyerhenke, Prutkin, Staudt,
                            triangles, and the clustering coefficient as the
                            fraction of closed triads; the mean local
                            coefficient beside it.
+* ``random_pairs`` / ``add_random_edges`` -- Sec. 4.2's graph with random
+                           long-range edges: uniform vertex pairs from a
+                           Philox stream of their own, merged into the CSR.
 
 Every function here is pinned by ``tests/test_oracle*.py`` to something other
 than itself (an independent Philox, mpmath, scipy quadrature, the paper's
@@ -96,6 +99,7 @@ def lib():
             L.orc_bands_ties.argtypes = [_P, _P, _P, _D, _I64, _P]
             L.orc_bands_ties.restype = _I64
             L.orc_degree_stats.argtypes = [_I64, _P, _I64, _P, _P]
+            L.orc_random_pairs.argtypes = [_I64, _I64, ctypes.c_uint64, _P, _P]
             L.orc_triangles.argtypes = [_I64, _P, _P, _P]
             L.orc_triangles.restype = _I64
             L.orc_num_threads.restype = ctypes.c_int
@@ -313,3 +317,40 @@ def graph_props(row_off, col_idx, d_min: int, triangles: bool = True) -> dict:
         local = np.where(pairs > 0, t / np.maximum(pairs, 1), 0.0)
         res["avg_local_clustering"] = float(local.sum() / n) if n > 0 else float("nan")
     return res
+
+
+def random_pairs(n: int, count: int, seed: int):
+    """The vertex pairs (u[count], v[count]) of the long-range edges."""
+    u = np.zeros(max(count, 1), dtype=np.int64)
+    v = np.zeros(max(count, 1), dtype=np.int64)
+    lib().orc_random_pairs(int(n), int(count), int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(u), _ptr(v))
+    return u[:count], v[:count]
+
+
+def add_random_edges(row_off, col_idx, count: int, seed: int):
+    """The CSR with the long-range edges of ``random_pairs`` added: the union
+    of the graph's edges and the drawn pairs (self-pairs dropped; a pair
+    drawn twice or already present is one edge).  Returns (row_off,
+    col_idx, added) with ``added`` the new undirected edges."""
+    off = np.asarray(row_off, dtype=np.int64)
+    col = np.asarray(col_idx, dtype=np.int64)
+    n = len(off) - 1
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(off))
+    u, v = random_pairs(n, count, seed)
+    keep = u != v
+    a = np.minimum(u[keep], v[keep])
+    b = np.maximum(u[keep], v[keep])
+    old = set(zip(rows[rows < col].tolist(), col[rows < col].tolist()))
+    new = set(zip(a.tolist(), b.tolist())) - old
+    if new:
+        na = np.fromiter((p[0] for p in new), dtype=np.int64, count=len(new))
+        nb = np.fromiter((p[1] for p in new), dtype=np.int64, count=len(new))
+        src = np.concatenate([rows, na, nb])
+        dst = np.concatenate([col, nb, na])
+    else:
+        src, dst = rows, col
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    out_off = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(src, minlength=n), out=out_off[1:])
+    return out_off, dst.astype(np.int32), len(new)

@@ -569,3 +569,26 @@ int64_t orc_triangles(int64_t n, const int64_t *row_off, const int32_t *col_idx,
     }
     return total;
 }
+
+/* ---------------------------------------------------------------------------
+ * Random long-range edges (Sec. 4.2 and the appendix on additional random
+ * edges: "adding 0.5 % of edges randomly").  Pair k draws the Philox4x32-10
+ * block at counter 2^63 + k, i.e. (k_lo, k_hi + 2^31, 0, 0), key (seed_lo,
+ * seed_hi) -- the point draws use counters below 2^31, so the two streams
+ * never meet -- and maps each 64-bit half w to the vertex floor(w n / 2^64)
+ * (the high word of the 128-bit product).  Self-pairs come out as u == v; the caller drops
+ * them, repeats and pairs already in the graph.
+ * ------------------------------------------------------------------------- */
+void orc_random_pairs(int64_t n, int64_t count, uint64_t seed, int64_t *u, int64_t *v)
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    for (int64_t k = 0; k < count; ++k) {
+        uint32_t ctr[4] = {(uint32_t)((uint64_t)k & 0xffffffffu), (uint32_t)((uint64_t)k >> 32) | 0x80000000u, 0u, 0u};
+        uint32_t x[4];
+        orc_philox4x32_10(ctr, key, x);
+        uint64_t a = ((uint64_t)x[0] << 32) | (uint64_t)x[1];
+        uint64_t b = ((uint64_t)x[2] << 32) | (uint64_t)x[3];
+        u[k] = (int64_t)(((unsigned __int128)a * (uint64_t)n) >> 64);
+        v[k] = (int64_t)(((unsigned __int128)b * (uint64_t)n) >> 64);
+    }
+}

@@ -23,6 +23,7 @@ EXPORTS = (
     "hrg_generate", "hrg_generate_host", "hrg_last_error", "hrg_version", "hrg_row_offsets_noalloc",
     "hrg_generate_batch_begin", "hrg_server_create", "hrg_server_submit", "hrg_server_wait", "hrg_server_release",
     "hrg_server_stats", "hrg_server_last_error", "hrg_server_destroy", "hrg_graph_props", "hrg_degree_histogram",
+    "hrg_add_random_edges",
 )
 HRG_PROPS_TRIANGLES = 0x1
 
@@ -118,6 +119,7 @@ def load(build_if_missing: bool = True):
         L.hrg_server_destroy.argtypes = [_P]
         L.hrg_graph_props.argtypes = [_P, _I64, _P, _P, _I64, ctypes.c_uint32, _P, ctypes.POINTER(hrg_props)]
         L.hrg_degree_histogram.argtypes = [_P, _I64, _P, _I64, _P, _P]
+        L.hrg_add_random_edges.argtypes = [_P, _I64, _P, _P, _I64, ctypes.c_uint64, _P, _P, _P, _I64, _PI64, _PI64]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         _lib = L
@@ -246,6 +248,29 @@ def degree_histogram(ctx: Context, row_off, max_degree: int, stream=None):
     ctx.check(L.hrg_degree_histogram(ctx.h, row_off.numel() - 1, _P(_dptr(row_off)), int(max_degree),
                                      _P(_dptr(hist)), _P(st.cuda_stream)))
     return hist
+
+
+def add_random_edges(ctx: Context, row_off, col_idx, count: int, seed: int, stream=None) -> dict:
+    """hrg_add_random_edges: the CSR with ``count`` random vertex pairs added
+    as edges (Sec. 4.2's long-range edges).  Returns row_off, col_idx (torch
+    tensors) and the number of added edges."""
+    import torch
+
+    L = load()
+    dev = torch.device("cuda", ctx.device)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    n = row_off.numel() - 1
+    old = int(row_off[-1].item() - row_off[0].item())
+    cap = old + 2 * int(count)
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    ne = ctypes.c_int64()
+    added = ctypes.c_int64()
+    src = _P(_dptr(col_idx)) if col_idx is not None and col_idx.numel() > 0 else _P(None)
+    ctx.check(L.hrg_add_random_edges(ctx.h, n, _P(_dptr(row_off)), src, int(count), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                     _P(st.cuda_stream), _P(_dptr(off)), _P(_dptr(col)), cap, ctypes.byref(ne),
+                                     ctypes.byref(added)))
+    return {"row_off": off, "col_idx": col[: ne.value], "added": added.value}
 
 
 class BatchItems:

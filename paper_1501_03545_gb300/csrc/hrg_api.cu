@@ -10,6 +10,7 @@
 
 #include "../../include/hrg.h"
 #include "hrg_internal.h"
+#include "hrg_graph_ops.h"
 
 using namespace hrg;
 
@@ -109,7 +110,8 @@ struct hrg_ctx {
            W_LIST2, W_LISTCNT, W_BIGTOT, W_SCAN, W_TMP, W_BUCKET, W_OUT_R, W_OUT_PHI, W_OUT_OFF, W_OUT_COL,
            W_HEAVY, W_CURSOR, W_SMALL, W_SMALLOFF, W_SMALLCUR, W_PLANS, W_NOFF, W_SOFF, W_GRAPHOF, W_HUBCNT,
            W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_POSOF, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
-           W_PACC, W_POUTDEG, W_POUTOFF, W_POUTCOL, W_PTRI, W_PSCAN,
+           W_PACC, W_POUTDEG, W_POUTOFF, W_POUTCOL, W_PTRI, W_PSCAN, W_LRCNT, W_LROFF, W_LRLIST, W_LRFIN,
+           W_LRDEG,
            W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
@@ -982,5 +984,67 @@ extern "C" int hrg_degree_histogram(hrg_ctx *ctx, int64_t n, const int64_t *row_
     CK(cudaMemcpyAsync(hflag, acc, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (*hflag) return set_err(ctx, HRG_EINVAL, "a degree exceeds max_degree = %lld", (long long)max_degree);
+    return HRG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Random long-range edges of Sec. 4.2 (kernels in hrg_longrange.cu).
+// ---------------------------------------------------------------------------
+extern "C" int hrg_add_random_edges(hrg_ctx *ctx, int64_t n, const int64_t *row_off, const int32_t *col_idx,
+                                    int64_t count, uint64_t seed, void *stream, int64_t *row_off_out,
+                                    int32_t *col_idx_out, int64_t col_capacity, int64_t *entries_out,
+                                    int64_t *added_out)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (n < 0 || n > 0x7fffffffLL) return set_err(ctx, HRG_EINVAL, "n must be in [0, 2^31)");
+    if (count < 0 || count > (1LL << 30)) return set_err(ctx, HRG_EINVAL, "count must be in [0, 2^30]");
+    if (!row_off || !row_off_out || !entries_out) return set_err(ctx, HRG_EINVAL, "null argument");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *hp = (char *)ctx->pinned;
+    CK(cudaMemcpyAsync(hp, row_off, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 8, row_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int64_t o0, on;
+    memcpy(&o0, hp, 8);
+    memcpy(&on, hp + 8, 8);
+    if (on > o0 && !col_idx) return set_err(ctx, HRG_EINVAL, "null col_idx");
+    if (n == 0) {
+        CK(cudaMemsetAsync(row_off_out, 0, sizeof(int64_t), st));
+        CK(cudaStreamSynchronize(st));
+        *entries_out = 0;
+        if (added_out) *added_out = 0;
+        return HRG_OK;
+    }
+    int rc;
+    void *cnt, *loff, *list, *fin, *ndeg, *scanws;
+    if ((rc = ensure(ctx, hrg_ctx::W_LRCNT, sizeof(int32_t) * n, &cnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_LROFF, sizeof(int64_t) * (n + 1), &loff))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_LRLIST, sizeof(int32_t) * (2 * count > 0 ? 2 * count : 1), &list))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_LRFIN, sizeof(int32_t) * n, &fin))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_LRDEG, sizeof(int32_t) * n, &ndeg))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_PSCAN, scan_workspace_bytes(n), &scanws))) return rc;
+    // partners of every vertex, listed
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n, st));
+    if (count > 0) CK(launch_lr_count(n, count, seed, (int32_t *)cnt, st));
+    CK(scan_i32_to_i64((const int32_t *)cnt, (int64_t *)loff, n, scanws, st));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n, st));
+    if (count > 0) CK(launch_lr_fill(n, count, seed, (const int64_t *)loff, (int32_t *)cnt, (int32_t *)list, st));
+    // new degrees and row offsets
+    CK(launch_lr_clean(n, row_off, col_idx, (const int64_t *)loff, (int32_t *)list, (int32_t *)fin, (int32_t *)ndeg,
+                       st));
+    CK(scan_i32_to_i64((const int32_t *)ndeg, row_off_out, n, scanws, st));
+    CK(cudaMemcpyAsync(hp + 16, row_off_out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int64_t ne;
+    memcpy(&ne, hp + 16, 8);
+    *entries_out = ne;
+    if (added_out) *added_out = (ne - (on - o0)) / 2;
+    if (ne > col_capacity || (ne > 0 && !col_idx_out))
+        return set_err(ctx, HRG_EOVERFLOW, "graph with the added edges has %lld entries, capacity %lld",
+                       (long long)ne, (long long)col_capacity);
+    CK(launch_lr_merge(n, row_off, col_idx, (const int64_t *)loff, (const int32_t *)list, (const int32_t *)fin,
+                       row_off_out, col_idx_out, st));
+    CK(cudaStreamSynchronize(st));
     return HRG_OK;
 }

@@ -49,23 +49,6 @@ int scan_launches(int64_t N);  // kernels one scan of length N launches
 cudaError_t scan_i32_to_i32(const int32_t *in, int32_t *out, int64_t N, void *ws, cudaStream_t s);
 cudaError_t scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t N, void *ws, cudaStream_t s);
 
-// ---- graph properties of Sec. 4.1 (hrg_props.cu) over a canonical CSR ----
-// acc_i[0..2] += largest degree (max), tail count, triads; acc_d[0] += tail log sum.
-cudaError_t launch_degree_stats(int64_t n, const int64_t *row_off, int64_t d_min, unsigned long long *acc_i,
-                                double *acc_d, cudaStream_t s);
-// hist[d] += vertices of degree d (hist zeroed by the caller); *overflow set if a degree exceeds max_degree.
-cudaError_t launch_degree_hist(int64_t n, const int64_t *row_off, int64_t max_degree, unsigned long long *hist,
-                               int *overflow, cudaStream_t s);
-// The neighbours ranked above each vertex (rank = (degree, id)): counts (fill = false) or lists (fill = true).
-cudaError_t launch_out_edges(int64_t n, const int64_t *row_off, const int32_t *col_idx, int32_t *out_deg,
-                             const int64_t *out_off, int32_t *out_col, bool fill, cudaStream_t s);
-// *total += triangles; t[v] += triangles at v (t may be null).
-cudaError_t launch_triangles(int64_t n, const int64_t *out_off, const int32_t *out_col, unsigned long long *t,
-                             unsigned long long *total, cudaStream_t s);
-// *acc += sum over v of t_v / (d_v (d_v - 1) / 2).
-cudaError_t launch_local_clustering(int64_t n, const int64_t *row_off, const unsigned long long *t, double *acc,
-                                    cudaStream_t s);
-
 // ---- queries (hrg_query.cu) and row sorts (hrg_sort.cu) ----
 constexpr int kRegRow = 32;       // rows up to this are sorted in registers by the write pass
 constexpr int kKeepRow = 64;      // rows up to this are kept by the count pass (no second traversal)

@@ -1,0 +1,182 @@
+// hrg_longrange.cu -- random long-range edges added to a generated graph.
+//
+// Sec. 4.2 (and the appendix on additional random edges) adds 0.5 % of the
+// edges between random vertex pairs, which shortens the diameter while the
+// other properties stay close.  Pair k draws the Philox4x32-10 block at
+// counter 2^63 + k, key = seed (the point draws use counters below 2^31),
+// and maps each 64-bit half w to the vertex floor(w n / 2^64).  Self-pairs,
+// pairs drawn twice and pairs already in the graph are dropped; the rest is
+// merged into a new canonical CSR:
+//   1. per vertex, the number of drawn partners (both endpoints of a pair);
+//   2. scan; the partners listed per vertex;
+//   3. per vertex (one thread: the lists hold ~2 count / n entries), the
+//      list sorted, repeats and present neighbours dropped, the new degree;
+//   4. scan of the new degrees (the caller's row offsets);
+//   5. per vertex (one warp), the old row and the new partners merged: each
+//      entry's place is its index plus the number of entries of the other
+//      list below it (a binary search).
+#include <algorithm>
+#include "hrg_common.cuh"
+#include "hrg_graph_ops.h"
+
+namespace hrg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarpsPerBlock = kThreads / 32;
+
+inline unsigned grid_for(int64_t items, int per_block)
+{
+    int64_t g = (items + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > (1 << 20)) g = 1 << 20;
+    return (unsigned)g;
+}
+
+__device__ __forceinline__ void random_pair(int64_t k, uint64_t seed, uint64_t n, int32_t &u, int32_t &v)
+{
+    const U4 w = philox_block((1ull << 63) | (uint64_t)k, seed);
+    const uint64_t a = ((uint64_t)w.x << 32) | w.y, b = ((uint64_t)w.z << 32) | w.w;
+    u = (int32_t)__umul64hi(a, n);
+    v = (int32_t)__umul64hi(b, n);
+}
+
+__global__ void k_lr_count(int64_t n, int64_t count, uint64_t seed, int32_t *__restrict__ cnt)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) {
+        int32_t u, v;
+        random_pair(k, seed, (uint64_t)n, u, v);
+        if (u == v) continue;
+        atomicAdd(cnt + u, 1);
+        atomicAdd(cnt + v, 1);
+    }
+}
+
+__global__ void k_lr_fill(int64_t n, int64_t count, uint64_t seed, const int64_t *__restrict__ loff,
+                          int32_t *__restrict__ cur, int32_t *__restrict__ list)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) {
+        int32_t u, v;
+        random_pair(k, seed, (uint64_t)n, u, v);
+        if (u == v) continue;
+        list[loff[u] + atomicAdd(cur + u, 1)] = v;
+        list[loff[v] + atomicAdd(cur + v, 1)] = u;
+    }
+}
+
+__device__ __forceinline__ bool in_sorted(const int32_t *__restrict__ a, int64_t len, int32_t x)
+{
+    int64_t lo = 0, hi = len;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < len && a[lo] == x;
+}
+
+// one thread per vertex: its drawn partners sorted (insertion), repeats and
+// present neighbours dropped, compacted; fin = partners kept, newdeg = d + fin
+__global__ void k_lr_clean(int64_t n, const int64_t *__restrict__ row_off, const int32_t *__restrict__ col_idx,
+                           const int64_t *__restrict__ loff, int32_t *__restrict__ list, int32_t *__restrict__ fin,
+                           int32_t *__restrict__ newdeg)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        int32_t *L = list + loff[v];
+        const int64_t c = loff[v + 1] - loff[v];
+        for (int64_t i = 1; i < c; ++i) {
+            const int32_t x = L[i];
+            int64_t j = i;
+            for (; j > 0 && L[j - 1] > x; --j) L[j] = L[j - 1];
+            L[j] = x;
+        }
+        const int64_t rb = row_off[v], d = row_off[v + 1] - rb;
+        int32_t kept = 0;
+        for (int64_t i = 0; i < c; ++i) {
+            const int32_t x = L[i];
+            if (i > 0 && x == L[i - 1]) continue;
+            if (in_sorted(col_idx + rb, d, x)) continue;
+            L[kept++] = x;
+        }
+        fin[v] = kept;
+        newdeg[v] = (int32_t)d + kept;
+    }
+}
+
+__device__ __forceinline__ int64_t count_below(const int32_t *__restrict__ a, int64_t len, int32_t x)
+{
+    int64_t lo = 0, hi = len;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// one warp per vertex: old row and kept partners merged into the new row
+__global__ void k_lr_merge(int64_t n, const int64_t *__restrict__ row_off, const int32_t *__restrict__ col_idx,
+                           const int64_t *__restrict__ loff, const int32_t *__restrict__ list,
+                           const int32_t *__restrict__ fin, const int64_t *__restrict__ row_off_out,
+                           int32_t *__restrict__ col_out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t v = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); v < n; v += nwarps) {
+        const int32_t *O = col_idx + row_off[v];
+        const int64_t d = row_off[v + 1] - row_off[v];
+        const int32_t *Nw = list + loff[v];
+        const int64_t f = fin[v];
+        int32_t *out = col_out + row_off_out[v];
+        if (f == 0) {
+            for (int64_t i = lane; i < d; i += 32) out[i] = O[i];
+            continue;
+        }
+        for (int64_t i = lane; i < d; i += 32) {
+            const int32_t x = O[i];
+            out[i + count_below(Nw, f, x)] = x;
+        }
+        for (int64_t j = lane; j < f; j += 32) {
+            const int32_t y = Nw[j];
+            out[j + count_below(O, d, y)] = y;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_lr_count(int64_t n, int64_t count, uint64_t seed, int32_t *cnt, cudaStream_t s)
+{
+    k_lr_count<<<std::min(grid_for(count, kThreads * 4), 152u * 16u), kThreads, 0, s>>>(n, count, seed, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lr_fill(int64_t n, int64_t count, uint64_t seed, const int64_t *loff, int32_t *cur, int32_t *list,
+                           cudaStream_t s)
+{
+    k_lr_fill<<<std::min(grid_for(count, kThreads * 4), 152u * 16u), kThreads, 0, s>>>(n, count, seed, loff, cur,
+                                                                                       list);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lr_clean(int64_t n, const int64_t *row_off, const int32_t *col_idx, const int64_t *loff,
+                            int32_t *list, int32_t *fin, int32_t *newdeg, cudaStream_t s)
+{
+    k_lr_clean<<<grid_for(n, kThreads * 4), kThreads, 0, s>>>(n, row_off, col_idx, loff, list, fin, newdeg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lr_merge(int64_t n, const int64_t *row_off, const int32_t *col_idx, const int64_t *loff,
+                            const int32_t *list, const int32_t *fin, const int64_t *row_off_out, int32_t *col_out,
+                            cudaStream_t s)
+{
+    k_lr_merge<<<grid_for(n, kWarpsPerBlock * 4), kThreads, 0, s>>>(n, row_off, col_idx, loff, list, fin,
+                                                                     row_off_out, col_out);
+    return cudaGetLastError();
+}
+
+}  // namespace hrg

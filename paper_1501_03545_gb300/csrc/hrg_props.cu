@@ -19,7 +19,7 @@
 //     (local clustering t_v / (d_v (d_v - 1) / 2)).
 #include <algorithm>
 #include <cstdio>
-#include "hrg_internal.h"
+#include "hrg_graph_ops.h"
 
 namespace hrg {
 
