@@ -147,6 +147,39 @@ def oracle_rate(n=ORACLE_SAMPLE_N):
             "seconds": dt}
 
 
+def quadtree_rate(H, ctx, stream, n=500_000):
+    """The paper's own generator (Algorithm 1 with the polar quadtree, from
+    the oracle package) on the host cores, and the device on the same
+    parameters: the 1e6-vertex workload's alpha, kbar and seed at n, where the
+    quadtree's Poincare-disk coordinates still resolve (R = 25.1)."""
+    import oracle as O
+    import torch
+
+    w = W.scaled(W.MEDIUM, n)
+    t0 = time.perf_counter()
+    R = O.solve_radius(w.n, w.alpha, w.kbar)
+    r, phi = O.sample(w.n, w.alpha, R, w.seed)
+    off, col, secs = O.quadtree_csr(r, phi, R, w.alpha, 64)
+    dt = time.perf_counter() - t0
+    ent = int(off[-1])
+    del r, phi, off, col
+    g = H.generate(ctx, w.n, w.alpha, w.kbar, w.seed, stream=stream)
+    gent = g["stats"]["n_entries"]
+    del g
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(3):
+        g = H.generate(ctx, w.n, w.alpha, w.kbar, w.seed, stream=stream)
+        del g
+    b.record(stream)
+    torch.cuda.synchronize()
+    gms = a.elapsed_time(b) / 3
+    return {"workload": w.name, "unit": UNIT, "leaf_capacity": 64, "cores": O.num_threads(),
+            "cpu_value": ent / dt, "cpu_seconds": dt, "cpu_seconds_build_count_fill": list(secs),
+            "cpu_entries": ent, "gpu_value": gent / (gms / 1e3), "gpu_ms": gms, "gpu_entries": gent}
+
+
 def replica_seed(w, rank):
     """Seed of rank's graph: every rank generates an independent graph of the
     same workload (no data-path collective; the path does not shard)."""
@@ -478,10 +511,11 @@ def main():
     qc = roof["query_csr_roofline"]
     qc["frac"] = qc["bytes"] / (qc["ms"] / 1e3) / 1e9 / peak
 
-    cpu = None
+    cpu = quadtree = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_rate(args.oracle_n)
         cpu.pop("seconds", None)
+        quadtree = quadtree_rate(H, ctx, stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -492,7 +526,7 @@ def main():
                            "undirected_edges_per_s": value / 2,
                            "l2": "no flush: every step writes and reads >8 GB, far above the 126 MB L2"},
                 "fp64_plain": fp64, "batched": batched, "serving": serving, "properties": props, "stage_ms": stage, "e2e": e2e, "roofline": roof, "clocks": clocks,
-                "cpu_baseline": cpu, "gpu_launches": last.get("launches", 0) * args.steps,
+                "cpu_baseline": cpu, "paper_quadtree": quadtree, "gpu_launches": last.get("launches", 0) * args.steps,
                 "job": {k: last[k] for k in ("R", "candidates", "rechecks", "bands", "hub_bands", "buckets",
                                              "hub_queries", "mid_rows", "big_rows", "mu")}}
         print(json.dumps(line), flush=True)

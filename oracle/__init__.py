@@ -24,6 +24,10 @@ Functions and the passage each follows (von Looz, Meyerhenke, Prutkin, Staudt,
                            triangles, and the clustering coefficient as the
                            fraction of closed triads; the mean local
                            coefficient beside it.
+* ``quadtree_csr``      -- the paper's own generator (Algorithm 1, the polar
+                           quadtree of Sec. 3, Proposition 1, Eq. (3)) from
+                           ``hrg_quadtree.c``: a second CPU baseline, checked
+                           against brute force, not the parity reference.
 * ``random_pairs`` / ``add_random_edges`` -- Sec. 4.2's graph with random
                            long-range edges: uniform vertex pairs from a
                            Philox stream of their own, merged into the CSR.
@@ -43,6 +47,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hrg_oracle.c")
+_SRC_QT = os.path.join(_HERE, "hrg_quadtree.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -56,10 +61,11 @@ _P = ctypes.c_void_p
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_QT))
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + ".tmp%d" % os.getpid()
         cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
+               "-shared", "-o", tmp, _SRC, _SRC_QT, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _SO)
     return _SO
@@ -100,6 +106,15 @@ def lib():
             L.orc_bands_ties.restype = _I64
             L.orc_degree_stats.argtypes = [_I64, _P, _I64, _P, _P]
             L.orc_random_pairs.argtypes = [_I64, _I64, ctypes.c_uint64, _P, _P]
+            L.orc_quadtree_build.argtypes = [_I64, _P, _P, _D, _D, ctypes.c_int32]
+            L.orc_quadtree_build.restype = _P
+            L.orc_quadtree_free.argtypes = [_P]
+            L.orc_quadtree_degrees.argtypes = [_P, _P]
+            L.orc_quadtree_degrees.restype = _I64
+            L.orc_quadtree_fill.argtypes = [_P, _P, _P]
+            L.orc_quadtree_circle.argtypes = [_D, _D, _D, _P]
+            L.orc_quadtree_depth_counts.argtypes = [_I64, _P, _P, _D, _D, ctypes.c_int32, ctypes.c_int32, _P]
+            L.orc_quadtree_depth_counts.restype = ctypes.c_int32
             L.orc_triangles.argtypes = [_I64, _P, _P, _P]
             L.orc_triangles.restype = _I64
             L.orc_num_threads.restype = ctypes.c_int
@@ -354,3 +369,46 @@ def add_random_edges(row_off, col_idx, count: int, seed: int):
     out_off = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(np.bincount(src, minlength=n), out=out_off[1:])
     return out_off, dst.astype(np.int32), len(new)
+
+
+def quadtree_csr(r, phi, R: float, alpha: float, capacity: int = 64):
+    """CSR of the paper's quadtree generator on the given points: (row_off,
+    col_idx, seconds) with seconds = (tree build, degree queries, row queries)."""
+    import time
+
+    r = _f64(r)
+    phi = _f64(phi)
+    n = len(r)
+    L = lib()
+    t0 = time.perf_counter()
+    h = L.orc_quadtree_build(n, _ptr(r), _ptr(phi), float(R), float(alpha), int(capacity))
+    try:
+        t1 = time.perf_counter()
+        deg = np.zeros(max(n, 1), dtype=np.int64)
+        L.orc_quadtree_degrees(h, _ptr(deg))
+        off = _offsets(deg[:n])
+        t2 = time.perf_counter()
+        col = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
+        L.orc_quadtree_fill(h, _ptr(off), _ptr(col))
+        t3 = time.perf_counter()
+    finally:
+        L.orc_quadtree_free(h)
+    return off, col[: int(off[-1])], (t1 - t0, t2 - t1, t3 - t2)
+
+
+def quadtree_depth_counts(r, phi, R: float, alpha: float, depth: int, capacity: int = 1):
+    """Points per cell of the quadtree's complete level ``depth`` (Lemma 4)."""
+    r = _f64(r)
+    phi = _f64(phi)
+    counts = np.zeros(4 ** depth, dtype=np.int64)
+    lib().orc_quadtree_depth_counts(len(r), _ptr(r), _ptr(phi), float(R), float(alpha), int(capacity), int(depth),
+                                    _ptr(counts))
+    return counts
+
+
+def quadtree_circle(R: float, phi: float, rh: float):
+    """Proposition 1: (centre radius, circle radius) in the Poincare disk of
+    the hyperbolic circle of radius R around (phi, rh)."""
+    out = np.zeros(2, dtype=np.float64)
+    lib().orc_quadtree_circle(float(R), float(phi), float(rh), _ptr(out))
+    return float(out[0]), float(out[1])
