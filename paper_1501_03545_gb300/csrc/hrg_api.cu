@@ -1043,8 +1043,8 @@ extern "C" int hrg_add_random_edges(hrg_ctx *ctx, int64_t n, const int64_t *row_
     if (ne > col_capacity || (ne > 0 && !col_idx_out))
         return set_err(ctx, HRG_EOVERFLOW, "graph with the added edges has %lld entries, capacity %lld",
                        (long long)ne, (long long)col_capacity);
-    CK(launch_lr_merge(n, row_off, col_idx, (const int64_t *)loff, (const int32_t *)list, (const int32_t *)fin,
-                       row_off_out, col_idx_out, st));
+    CK(launch_lr_merge(n, on - o0, row_off, col_idx, (const int64_t *)loff, (const int32_t *)list,
+                       (const int32_t *)fin, row_off_out, col_idx_out, st));
     CK(cudaStreamSynchronize(st));
     return HRG_OK;
 }

@@ -33,9 +33,9 @@ cudaError_t launch_lr_fill(int64_t n, int64_t count, uint64_t seed, const int64_
 // Partner lists sorted, repeats and present neighbours dropped: fin[v] kept, newdeg[v] = d_v + fin[v].
 cudaError_t launch_lr_clean(int64_t n, const int64_t *row_off, const int32_t *col_idx, const int64_t *loff,
                             int32_t *list, int32_t *fin, int32_t *newdeg, cudaStream_t s);
-// New rows: old row and kept partners merged, at row_off_out.
-cudaError_t launch_lr_merge(int64_t n, const int64_t *row_off, const int32_t *col_idx, const int64_t *loff,
-                            const int32_t *list, const int32_t *fin, const int64_t *row_off_out, int32_t *col_out,
-                            cudaStream_t s);
+// New rows: old rows (old_entries = row_off[n] - row_off[0]) and kept partners merged, at row_off_out.
+cudaError_t launch_lr_merge(int64_t n, int64_t old_entries, const int64_t *row_off, const int32_t *col_idx,
+                            const int64_t *loff, const int32_t *list, const int32_t *fin, const int64_t *row_off_out,
+                            int32_t *col_out, cudaStream_t s);
 
 }  // namespace hrg

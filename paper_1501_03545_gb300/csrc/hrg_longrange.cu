@@ -12,9 +12,13 @@
 //   3. per vertex (one thread: the lists hold ~2 count / n entries), the
 //      list sorted, repeats and present neighbours dropped, the new degree;
 //   4. scan of the new degrees (the caller's row offsets);
-//   5. per vertex (one warp), the old row and the new partners merged: each
-//      entry's place is its index plus the number of entries of the other
-//      list below it (a binary search).
+//   5. the old rows and the new partners merged: an old entry's place is its
+//      row's new offset plus its index in the row plus the number of the
+//      row's new partners below it; a new partner's, the new offset plus its
+//      index plus the number of old entries below it (binary searches).  The
+//      old entries are walked as one flat array in chunks of kRun per lane
+//      (a warp finds its chunk's rows once), so a row of millions of entries
+//      is spread over many warps.
 #include <algorithm>
 #include "hrg_common.cuh"
 #include "hrg_graph_ops.h"
@@ -118,31 +122,73 @@ __device__ __forceinline__ int64_t count_below(const int32_t *__restrict__ a, in
     return lo;
 }
 
-// one warp per vertex: old row and kept partners merged into the new row
-__global__ void k_lr_merge(int64_t n, const int64_t *__restrict__ row_off, const int32_t *__restrict__ col_idx,
-                           const int64_t *__restrict__ loff, const int32_t *__restrict__ list,
-                           const int32_t *__restrict__ fin, const int64_t *__restrict__ row_off_out,
-                           int32_t *__restrict__ col_out)
+constexpr int kRun = 32;  // old entries per lane of the flat merge
+
+// the last v in [lo, hi] with row_off[v] <= q (row_off[lo] <= q assumed)
+__device__ __forceinline__ int64_t row_of(const int64_t *__restrict__ row_off, int64_t lo, int64_t hi, int64_t q)
+{
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (row_off[mid] <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// old entries at their new places; warp chunk = 32 * kRun entries, lane run = kRun
+__global__ void k_lr_merge_old(int64_t n, const int64_t *__restrict__ row_off, const int32_t *__restrict__ col_idx,
+                               const int64_t *__restrict__ loff, const int32_t *__restrict__ list,
+                               const int32_t *__restrict__ fin, const int64_t *__restrict__ row_off_out,
+                               int32_t *__restrict__ col_out)
 {
     const int lane = threadIdx.x & 31;
+    const int64_t base = row_off[0], total = row_off[n] - base;
+    const int64_t chunk = 32 * (int64_t)kRun;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t v = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); v < n; v += nwarps) {
+    for (int64_t c0 = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * chunk; c0 < total;
+         c0 += nwarps * chunk) {
+        // rows of the chunk's first and last entries, once per warp
+        int64_t v_lo = 0, v_hi = 0;
+        if (lane == 0) v_lo = row_of(row_off, 0, n - 1, base + c0);
+        if (lane == 31) v_hi = row_of(row_off, 0, n - 1, base + min(c0 + chunk, total) - 1);
+        v_lo = __shfl_sync(0xffffffffu, v_lo, 0);
+        v_hi = __shfl_sync(0xffffffffu, v_hi, 31);
+        const int64_t p0 = c0 + (int64_t)lane * kRun;
+        if (p0 >= total) continue;
+        const int64_t p1 = min(p0 + (int64_t)kRun, total);
+        int64_t v = row_of(row_off, v_lo, v_hi, base + p0);
+        int64_t rb = row_off[v], re = row_off[v + 1];
+        for (int64_t p = p0; p < p1; ++p) {
+            const int64_t q = base + p;
+            while (q >= re) {  // past the row's end (empty rows skipped)
+                ++v;
+                rb = re;
+                re = row_off[v + 1];
+            }
+            const int32_t x = col_idx[q];
+            const int64_t f = fin[v];
+            const int64_t shift = f ? count_below(list + loff[v], f, x) : 0;
+            col_out[row_off_out[v] + (q - rb) + shift] = x;
+        }
+    }
+}
+
+// kept partners at their new places (one thread per vertex)
+__global__ void k_lr_merge_new(int64_t n, const int64_t *__restrict__ row_off, const int32_t *__restrict__ col_idx,
+                               const int64_t *__restrict__ loff, const int32_t *__restrict__ list,
+                               const int32_t *__restrict__ fin, const int64_t *__restrict__ row_off_out,
+                               int32_t *__restrict__ col_out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t f = fin[v];
+        if (f == 0) continue;
         const int32_t *O = col_idx + row_off[v];
         const int64_t d = row_off[v + 1] - row_off[v];
         const int32_t *Nw = list + loff[v];
-        const int64_t f = fin[v];
-        int32_t *out = col_out + row_off_out[v];
-        if (f == 0) {
-            for (int64_t i = lane; i < d; i += 32) out[i] = O[i];
-            continue;
-        }
-        for (int64_t i = lane; i < d; i += 32) {
-            const int32_t x = O[i];
-            out[i + count_below(Nw, f, x)] = x;
-        }
-        for (int64_t j = lane; j < f; j += 32) {
+        for (int64_t j = 0; j < f; ++j) {
             const int32_t y = Nw[j];
-            out[j + count_below(O, d, y)] = y;
+            col_out[row_off_out[v] + j + count_below(O, d, y)] = y;
         }
     }
 }
@@ -170,12 +216,15 @@ cudaError_t launch_lr_clean(int64_t n, const int64_t *row_off, const int32_t *co
     return cudaGetLastError();
 }
 
-cudaError_t launch_lr_merge(int64_t n, const int64_t *row_off, const int32_t *col_idx, const int64_t *loff,
-                            const int32_t *list, const int32_t *fin, const int64_t *row_off_out, int32_t *col_out,
-                            cudaStream_t s)
+cudaError_t launch_lr_merge(int64_t n, int64_t old_entries, const int64_t *row_off, const int32_t *col_idx,
+                            const int64_t *loff, const int32_t *list, const int32_t *fin, const int64_t *row_off_out,
+                            int32_t *col_out, cudaStream_t s)
 {
-    k_lr_merge<<<grid_for(n, kWarpsPerBlock * 4), kThreads, 0, s>>>(n, row_off, col_idx, loff, list, fin,
-                                                                     row_off_out, col_out);
+    if (old_entries > 0)
+        k_lr_merge_old<<<std::min(grid_for(old_entries, kThreads * kRun), 152u * 16u), kThreads, 0, s>>>(
+            n, row_off, col_idx, loff, list, fin, row_off_out, col_out);
+    k_lr_merge_new<<<grid_for(n, kThreads * 4), kThreads, 0, s>>>(n, row_off, col_idx, loff, list, fin, row_off_out,
+                                                                 col_out);
     return cudaGetLastError();
 }
 
