@@ -355,6 +355,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     b.small_cursor = (unsigned long long *)small_cur;
     b.small_cap = small_cap;
 
+    char *hp = (char *)ctx->pinned;
     for (int attempt = 0;; ++attempt) {
         if ((rc = ensure(ctx, hrg_ctx::W_HEAVY, sizeof(int4) * heavy_cap, &heavy))) return rc;
         if ((rc = ensure(ctx, hrg_ctx::W_SEGCNT, sizeof(int32_t) * heavy_cap, &scnt))) return rc;
@@ -371,24 +372,24 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
         CK(cudaEventRecord(ctx->ev[3], st));
         CK(launch_count_rim(p, b, J.fp64, st));
         CK(cudaEventRecord(ctx->ev[4], st));
-        if (J.p_hub == 0) break;
-        int32_t *hc = (int32_t *)ctx->pinned;
-        CK(cudaMemcpyAsync(hc, (int32_t *)listcnt + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (*hc <= heavy_cap) break;
-        if (attempt > 0 || *hc > (1 << 30)) return set_err(ctx, HRG_EINTERNAL, "heavy segment list overflow");
-        heavy_cap = (int64_t)*hc + *hc / 8 + 1024;  // grow and count again
-    }
 
-    // 4. row offsets
-    CK(scan_i32_to_i64((int32_t *)deg, row_off_out, n, scanws, st));
-    CK(cudaEventRecord(ctx->ev[5], st));
-    char *hp = (char *)ctx->pinned;
-    CK(cudaMemcpyAsync(hp + 0, row_off_out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(hp + 8, listcnt, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(hp + 24, bigtot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(hp + 64, stats, sizeof(uint64_t) * 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+        // 4. row offsets; the totals, the list lengths (the heavy hub
+        // segments among them) and the counters come back together
+        CK(scan_i32_to_i64((int32_t *)deg, row_off_out, n, scanws, st));
+        CK(cudaEventRecord(ctx->ev[5], st));
+        CK(cudaMemcpyAsync(hp + 0, row_off_out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hp + 8, listcnt, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hp + 24, bigtot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hp + 64, stats, sizeof(uint64_t) * 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        int32_t heavy_found;
+        memcpy(&heavy_found, hp + 8 + 12, 4);
+        if (J.p_hub == 0 || heavy_found <= heavy_cap) break;
+        // the heavy hub segments did not fit: the degrees are incomplete, so
+        // grow the list and count again
+        if (attempt > 0 || heavy_found > (1 << 30)) return set_err(ctx, HRG_EINTERNAL, "heavy segment list overflow");
+        heavy_cap = (int64_t)heavy_found + heavy_found / 8 + 1024;
+    }
     memcpy(&J.n_entries, hp + 0, 8);
     memcpy(J.lists, hp + 8, 12);
     memcpy(&J.big_total, hp + 24, 8);
