@@ -263,8 +263,10 @@ def run_properties(H, ctx, stream, graphs):
     exponent, triads, triangles, clustering) of freshly generated graphs, and
     Sec. 4.2's random long-range edges (hrg_add_random_edges, 0.5 % of m),
     each timed as the host wall time of the call (after one warm-up call up
-    to n = 1e7; the calls return with their results).  graphs: (workload,
-    seed, d_min, properties of the graph with the long-range edges too)."""
+    to n = 1e7; the calls return with their results), and the diameter
+    bounds of Sec. 4.1 by double sweeps (hrg_diameter_bounds).  graphs:
+    (workload, seed, d_min, properties and diameter of the graph with the
+    long-range edges too)."""
     import torch
 
     def timed(f, warm):
@@ -282,6 +284,9 @@ def run_properties(H, ctx, stream, graphs):
         p, ms = timed(lambda: H.graph_props(ctx, g["row_off"], g["col_idx"], d_min=d_min, stream=stream), warm)
         p["ms"] = ms
         p["gamma_expected"] = 2 * w.alpha + 1
+        (lo, hi, _, size), dms = timed(lambda: H.diameter_bounds(ctx, g["row_off"], g["col_idx"], stream=stream),
+                                       False)
+        p["diameter"] = {"lower": lo, "upper": hi, "component": size, "ms": dms}
         count = -(-p["entries"] // 400)  # ceil(0.005 m), m = entries / 2
         lr, lms = timed(lambda: H.add_random_edges(ctx, g["row_off"], g["col_idx"], count, 99, stream=stream), True)
         del g
@@ -289,6 +294,8 @@ def run_properties(H, ctx, stream, graphs):
         if lr_props:
             q = H.graph_props(ctx, lr["row_off"], lr["col_idx"], d_min=d_min, stream=stream)
             p["long_range"].update({k: q[k] for k in ("gamma", "triangles", "clustering", "avg_local_clustering")})
+            lo, hi, _, size = H.diameter_bounds(ctx, lr["row_off"], lr["col_idx"], stream=stream)
+            p["long_range"]["diameter"] = {"lower": lo, "upper": hi, "component": size}
         del lr
         out[w.name] = p
     return out
@@ -487,7 +494,9 @@ def main():
     # study) and the timed graph
     props = None
     if not args.no_props and rank == 0:
-        props = run_properties(H, ctx, stream, [(W.MEDIUM, W.MEDIUM.seed, 30, True), (w, seed, 48, False)])
+        gamma3 = W.Workload("rhg_n2e5_a1.0_k10", 200_000, 1.0, 10.0, 4)  # gamma = 3, average degree 10
+        props = run_properties(H, ctx, stream, [(W.MEDIUM, W.MEDIUM.seed, 30, True), (gamma3, gamma3.seed, 30, True),
+                                                (w, seed, 48, False)])
 
     # roofline of the dominant kernel: the rim count pass (k_rim_sector), one
     # launch per graph, timed by the library's CUDA events around exactly that

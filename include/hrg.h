@@ -311,6 +311,39 @@ int hrg_add_random_edges(hrg_ctx *ctx, int64_t n, const int64_t *row_off, const 
                          int64_t col_capacity, int64_t *entries_out, int64_t *added_out);
 
 /*
+ * hrg_bfs -- breadth-first search over a CSR (as for hrg_graph_props), for
+ * the diameter of Sec. 4.1 (the longest shortest path) that Sec. 4.2's
+ * long-range edges shorten.
+ *   source   vertex to start from, or -1 for the vertex of highest degree
+ *            (lowest id among ties)
+ *   dist     device int32[n] (caller owned): hops from the source, -1 where
+ *            unreached
+ *   *ecc_out the source's eccentricity in its component; *reached_out
+ *            (may be null) the component's size; *far_out (may be null) the
+ *            lowest id at distance ecc; *source_out (may be null) the source
+ *   stream   cudaStream_t (as void*); the call returns when done (one
+ *            read-back per level)
+ * Errors: HRG_EINVAL (n outside [1, 2^31), source >= n, null pointer),
+ * HRG_ENOMEM, HRG_ECUDA.
+ */
+int hrg_bfs(hrg_ctx *ctx, int64_t n, const int64_t *row_off, const int32_t *col_idx, int64_t source, void *stream,
+            int32_t *dist, int32_t *ecc_out, int64_t *reached_out, int64_t *far_out, int64_t *source_out);
+
+/*
+ * hrg_diameter_bounds -- lower <= diameter <= upper for the component of the
+ * highest-degree vertex, by repeated double sweeps: a search from root r
+ * gives ecc(r) <= diameter <= 2 ecc(r); the first root is the vertex of
+ * highest degree (lowest id among ties), each next root the previous search's
+ * farthest vertex (lowest id among ties), at most `sweeps` searches (1..64),
+ * stopping when the farthest vertex is the root.  *component (may be null)
+ * is the component's size; roots (host int64[sweeps], may be null) receives
+ * the roots used, -1 after the last.
+ * Errors as hrg_bfs, and HRG_EINVAL for sweeps outside [1, 64].
+ */
+int hrg_diameter_bounds(hrg_ctx *ctx, int64_t n, const int64_t *row_off, const int32_t *col_idx, int32_t sweeps,
+                        void *stream, int32_t *lower, int32_t *upper, int64_t *component, int64_t *roots);
+
+/*
  * Request server -- generation requests of different sizes and parameters on
  * one GPU with continuous batching.  The paper has no serving layer; this is
  * the request loop around Algorithm 1 for callers that submit many graphs.

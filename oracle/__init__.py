@@ -28,6 +28,11 @@ Functions and the passage each follows (von Looz, Meyerhenke, Prutkin, Staudt,
                            quadtree of Sec. 3, Proposition 1, Eq. (3)) from
                            ``hrg_quadtree.c``: a second CPU baseline, checked
                            against brute force, not the parity reference.
+* ``bfs`` / ``diameter_bounds`` -- hop distances from one vertex; the
+                           diameter of a vertex's component bracketed by
+                           repeated double sweeps (Sec. 4.1's longest
+                           shortest path, which Sec. 4.2's long-range edges
+                           shorten).
 * ``random_pairs`` / ``add_random_edges`` -- Sec. 4.2's graph with random
                            long-range edges: uniform vertex pairs from a
                            Philox stream of their own, merged into the CSR.
@@ -113,6 +118,8 @@ def lib():
             L.orc_quadtree_degrees.restype = _I64
             L.orc_quadtree_fill.argtypes = [_P, _P, _P]
             L.orc_quadtree_circle.argtypes = [_D, _D, _D, _P]
+            L.orc_bfs.argtypes = [_I64, _P, _P, _I64, _P]
+            L.orc_bfs.restype = ctypes.c_int32
             L.orc_quadtree_depth_counts.argtypes = [_I64, _P, _P, _D, _D, ctypes.c_int32, ctypes.c_int32, _P]
             L.orc_quadtree_depth_counts.restype = ctypes.c_int32
             L.orc_triangles.argtypes = [_I64, _P, _P, _P]
@@ -412,3 +419,41 @@ def quadtree_circle(R: float, phi: float, rh: float):
     out = np.zeros(2, dtype=np.float64)
     lib().orc_quadtree_circle(float(R), float(phi), float(rh), _ptr(out))
     return float(out[0]), float(out[1])
+
+
+def bfs(row_off, col_idx, source: int):
+    """(dist int32[n] with -1 where unreached, eccentricity of source)."""
+    off = np.ascontiguousarray(np.asarray(row_off, dtype=np.int64))
+    col = np.ascontiguousarray(np.asarray(col_idx, dtype=np.int32))
+    n = len(off) - 1
+    dist = np.zeros(max(n, 1), dtype=np.int32)
+    colp = col if len(col) else np.zeros(1, dtype=np.int32)
+    ecc = int(lib().orc_bfs(n, _ptr(off), _ptr(colp), int(source), _ptr(dist)))
+    return dist[:n], ecc
+
+
+def diameter_bounds(row_off, col_idx, sweeps: int = 4, bfs_fn=None):
+    """Bounds on the diameter of the component of the highest-degree vertex
+    (lowest id among ties) by repeated double sweeps: BFS from a root gives
+    ecc(root) <= diameter <= 2 ecc(root); the next root is the farthest
+    vertex (lowest id among ties).  Returns (lower, upper, roots, component
+    size).  bfs_fn(source) -> (dist, ecc) may replace the oracle's BFS, so
+    that the device's search is driven by the same rule."""
+    off = np.asarray(row_off, dtype=np.int64)
+    if bfs_fn is None:
+        bfs_fn = lambda s: bfs(row_off, col_idx, s)  # noqa: E731
+    deg = np.diff(off)
+    root = int(np.argmax(deg))
+    lower, upper, roots, size = 0, None, [], 0
+    for _ in range(sweeps):
+        dist, ecc = bfs_fn(root)
+        dist = np.asarray(dist)
+        roots.append(root)
+        size = int((dist >= 0).sum())
+        lower = max(lower, ecc)
+        upper = 2 * ecc if upper is None else min(upper, 2 * ecc)
+        far = int(np.flatnonzero(dist == ecc)[0])
+        if far == root:
+            break
+        root = far
+    return lower, upper, roots, size

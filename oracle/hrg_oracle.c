@@ -592,3 +592,33 @@ void orc_random_pairs(int64_t n, int64_t count, uint64_t seed, int64_t *u, int64
         v[k] = (int64_t)(((unsigned __int128)b * (uint64_t)n) >> 64);
     }
 }
+
+/* ---------------------------------------------------------------------------
+ * Breadth-first search (Sec. 4.1: the diameter is the longest shortest path;
+ * Sec. 4.2: long-range edges shorten it).  dist[v] = hops from source, -1
+ * where unreached; returns the eccentricity of source in its component.
+ * ------------------------------------------------------------------------- */
+int32_t orc_bfs(int64_t n, const int64_t *row_off, const int32_t *col_idx, int64_t source, int32_t *dist)
+{
+    for (int64_t v = 0; v < n; ++v) dist[v] = -1;
+    if (n == 0) return 0;
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t head = 0, tail = 0;
+    dist[source] = 0;
+    queue[tail++] = (int32_t)source;
+    int32_t ecc = 0;
+    while (head < tail) {
+        const int32_t u = queue[head++];
+        const int32_t du = dist[u];
+        if (du > ecc) ecc = du;
+        for (int64_t k = row_off[u]; k < row_off[u + 1]; ++k) {
+            const int32_t w = col_idx[k];
+            if (dist[w] < 0) {
+                dist[w] = du + 1;
+                queue[tail++] = w;
+            }
+        }
+    }
+    free(queue);
+    return ecc;
+}

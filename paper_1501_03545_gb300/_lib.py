@@ -23,7 +23,7 @@ EXPORTS = (
     "hrg_generate", "hrg_generate_host", "hrg_last_error", "hrg_version", "hrg_row_offsets_noalloc",
     "hrg_generate_batch_begin", "hrg_server_create", "hrg_server_submit", "hrg_server_wait", "hrg_server_release",
     "hrg_server_stats", "hrg_server_last_error", "hrg_server_destroy", "hrg_graph_props", "hrg_degree_histogram",
-    "hrg_add_random_edges",
+    "hrg_add_random_edges", "hrg_bfs", "hrg_diameter_bounds",
 )
 HRG_PROPS_TRIANGLES = 0x1
 
@@ -119,6 +119,9 @@ def load(build_if_missing: bool = True):
         L.hrg_server_destroy.argtypes = [_P]
         L.hrg_graph_props.argtypes = [_P, _I64, _P, _P, _I64, ctypes.c_uint32, _P, ctypes.POINTER(hrg_props)]
         L.hrg_degree_histogram.argtypes = [_P, _I64, _P, _I64, _P, _P]
+        L.hrg_bfs.argtypes = [_P, _I64, _P, _P, _I64, _P, _P, ctypes.POINTER(ctypes.c_int32), _PI64, _PI64, _PI64]
+        L.hrg_diameter_bounds.argtypes = [_P, _I64, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32), _PI64, _PI64]
         L.hrg_add_random_edges.argtypes = [_P, _I64, _P, _P, _I64, ctypes.c_uint64, _P, _P, _P, _I64, _PI64, _PI64]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
@@ -271,6 +274,41 @@ def add_random_edges(ctx: Context, row_off, col_idx, count: int, seed: int, stre
                                      _P(st.cuda_stream), _P(_dptr(off)), _P(_dptr(col)), cap, ctypes.byref(ne),
                                      ctypes.byref(added)))
     return {"row_off": off, "col_idx": col[: ne.value], "added": added.value}
+
+
+def bfs(ctx: Context, row_off, col_idx, source: int, stream=None):
+    """hrg_bfs: (dist int32 tensor, eccentricity, component size, farthest
+    vertex, source used); source -1 starts at the highest-degree vertex."""
+    import torch
+
+    L = load()
+    dev = torch.device("cuda", ctx.device)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    n = row_off.numel() - 1
+    dist = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    ecc = ctypes.c_int32()
+    reached, far, src = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    col = _P(_dptr(col_idx)) if col_idx is not None and col_idx.numel() > 0 else _P(None)
+    ctx.check(L.hrg_bfs(ctx.h, n, _P(_dptr(row_off)), col, int(source), _P(st.cuda_stream), _P(_dptr(dist)),
+                        ctypes.byref(ecc), ctypes.byref(reached), ctypes.byref(far), ctypes.byref(src)))
+    return dist[:n], ecc.value, reached.value, far.value, src.value
+
+
+def diameter_bounds(ctx: Context, row_off, col_idx, sweeps: int = 4, stream=None):
+    """hrg_diameter_bounds: (lower, upper, roots, component size)."""
+    import torch
+
+    L = load()
+    dev = torch.device("cuda", ctx.device)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    n = row_off.numel() - 1
+    lo, hi = ctypes.c_int32(), ctypes.c_int32()
+    size = ctypes.c_int64()
+    roots = (ctypes.c_int64 * sweeps)()
+    col = _P(_dptr(col_idx)) if col_idx is not None and col_idx.numel() > 0 else _P(None)
+    ctx.check(L.hrg_diameter_bounds(ctx.h, n, _P(_dptr(row_off)), col, int(sweeps), _P(st.cuda_stream),
+                                    ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(size), roots))
+    return lo.value, hi.value, [r for r in roots if r >= 0], size.value
 
 
 class BatchItems:

@@ -111,7 +111,7 @@ struct hrg_ctx {
            W_HEAVY, W_CURSOR, W_SMALL, W_SMALLOFF, W_SMALLCUR, W_PLANS, W_NOFF, W_SOFF, W_GRAPHOF, W_HUBCNT,
            W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_POSOF, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
            W_PACC, W_POUTDEG, W_POUTOFF, W_POUTCOL, W_PTRI, W_PSCAN, W_LRCNT, W_LROFF, W_LRLIST, W_LRFIN,
-           W_LRDEG,
+           W_LRDEG, W_BFSF0, W_BFSF1, W_BFSDEG, W_BFSOFF, W_BFSACC, W_BFSDIST,
            W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
@@ -1047,5 +1047,108 @@ extern "C" int hrg_add_random_edges(hrg_ctx *ctx, int64_t n, const int64_t *row_
     CK(launch_lr_merge(n, on - o0, row_off, col_idx, (const int64_t *)loff, (const int32_t *)list,
                        (const int32_t *)fin, row_off_out, col_idx_out, st));
     CK(cudaStreamSynchronize(st));
+    return HRG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Breadth-first search and diameter bounds (Sec. 4.1, Sec. 4.2; kernels in
+// hrg_bfs.cu).
+// ---------------------------------------------------------------------------
+extern "C" int hrg_bfs(hrg_ctx *ctx, int64_t n, const int64_t *row_off, const int32_t *col_idx, int64_t source,
+                       void *stream, int32_t *dist, int32_t *ecc_out, int64_t *reached_out, int64_t *far_out,
+                       int64_t *source_out)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (n < 1 || n > 0x7fffffffLL) return set_err(ctx, HRG_EINVAL, "n must be in [1, 2^31)");
+    if (source >= n) return set_err(ctx, HRG_EINVAL, "source must be < n");
+    if (!row_off || !dist || !ecc_out) return set_err(ctx, HRG_EINVAL, "null argument");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *hp = (char *)ctx->pinned;
+    CK(cudaMemcpyAsync(hp, row_off, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 8, row_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int64_t o0, on;
+    memcpy(&o0, hp, 8);
+    memcpy(&on, hp + 8, 8);
+    if (on > o0 && !col_idx) return set_err(ctx, HRG_EINVAL, "null col_idx");
+    int rc;
+    void *f0, *f1, *fdeg, *foff, *acc, *scanws;
+    if ((rc = ensure(ctx, hrg_ctx::W_BFSF0, sizeof(int32_t) * n, &f0))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_BFSF1, sizeof(int32_t) * n, &f1))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_BFSDEG, sizeof(int32_t) * n, &fdeg))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_BFSOFF, sizeof(int64_t) * (n + 1), &foff))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_BFSACC, 64, &acc))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_PSCAN, scan_workspace_bytes(n), &scanws))) return rc;
+    unsigned long long *best = (unsigned long long *)acc;        // [0]
+    int32_t *nnext = (int32_t *)((char *)acc + 8);               // [8]
+    int32_t *far = (int32_t *)((char *)acc + 12);                // [12]
+    int64_t *src = (int64_t *)((char *)acc + 16);                // [16]
+    CK(cudaMemsetAsync(acc, 0, 64, st));
+    CK(launch_bfs_init(n, dist, row_off, best, st));
+    CK(launch_bfs_seed(best, source, dist, (int32_t *)f0, src, far, st));
+    int32_t *cur = (int32_t *)f0, *nxt = (int32_t *)f1;
+    int32_t fsize = 1, level = 0;
+    int64_t reached = 1;
+    for (;;) {
+        CK(launch_bfs_frontier_deg(fsize, cur, row_off, (int32_t *)fdeg, st));
+        CK(scan_i32_to_i64((const int32_t *)fdeg, (int64_t *)foff, fsize, scanws, st));
+        CK(cudaMemsetAsync(nnext, 0, sizeof(int32_t), st));
+        CK(launch_bfs_expand(level, fsize, cur, (const int64_t *)foff, row_off, col_idx, dist, nxt, nnext, st));
+        CK(cudaMemcpyAsync(hp + 16, nnext, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        int32_t got;
+        memcpy(&got, hp + 16, 4);
+        if (got == 0) break;
+        reached += got;
+        fsize = got;
+        ++level;
+        std::swap(cur, nxt);
+    }
+    CK(launch_bfs_far(n, dist, level, far, st));
+    CK(cudaMemcpyAsync(hp + 24, acc, 24, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int32_t hfar;
+    int64_t hsrc;
+    memcpy(&hfar, hp + 24 + 12, 4);
+    memcpy(&hsrc, hp + 24 + 16, 8);
+    *ecc_out = level;
+    if (reached_out) *reached_out = reached;
+    if (far_out) *far_out = hfar;
+    if (source_out) *source_out = hsrc;
+    return HRG_OK;
+}
+
+extern "C" int hrg_diameter_bounds(hrg_ctx *ctx, int64_t n, const int64_t *row_off, const int32_t *col_idx,
+                                   int32_t sweeps, void *stream, int32_t *lower, int32_t *upper,
+                                   int64_t *component, int64_t *roots)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (n < 1 || n > 0x7fffffffLL) return set_err(ctx, HRG_EINVAL, "n must be in [1, 2^31)");
+    if (sweeps < 1 || sweeps > 64) return set_err(ctx, HRG_EINVAL, "sweeps must be in [1, 64]");
+    if (!lower || !upper) return set_err(ctx, HRG_EINVAL, "null argument");
+    int rc;
+    void *dist;
+    if ((rc = ensure(ctx, hrg_ctx::W_BFSDIST, sizeof(int32_t) * n, &dist))) return rc;
+    int64_t root = -1;
+    int32_t lo = 0, hi = INT32_MAX;
+    int64_t size = 0;
+    if (roots)
+        for (int32_t k = 0; k < sweeps; ++k) roots[k] = -1;
+    for (int32_t k = 0; k < sweeps; ++k) {
+        int32_t ecc;
+        int64_t reached, far, src;
+        if ((rc = hrg_bfs(ctx, n, row_off, col_idx, root, stream, (int32_t *)dist, &ecc, &reached, &far, &src)))
+            return rc;
+        if (roots) roots[k] = src;
+        size = reached;
+        lo = std::max(lo, ecc);
+        hi = std::min(hi, 2 * ecc);
+        if (far == src) break;
+        root = far;
+    }
+    *lower = lo;
+    *upper = hi;
+    if (component) *component = size;
     return HRG_OK;
 }

@@ -38,4 +38,20 @@ cudaError_t launch_lr_merge(int64_t n, int64_t old_entries, const int64_t *row_o
                             const int64_t *loff, const int32_t *list, const int32_t *fin, const int64_t *row_off_out,
                             int32_t *col_out, cudaStream_t s);
 
+// ---- breadth-first search (hrg_bfs.cu) ----
+// dist[v] = -1; *best = max over v of (degree << 31 | (2^31 - 1 - v)) (best zeroed by the caller).
+cudaError_t launch_bfs_init(int64_t n, int32_t *dist, const int64_t *row_off, unsigned long long *best,
+                            cudaStream_t s);
+// The source (or, for source < 0, the vertex *best names) at distance 0, alone in frontier; *far = INT_MAX.
+cudaError_t launch_bfs_seed(const unsigned long long *best, int64_t source, int32_t *dist, int32_t *frontier,
+                            int64_t *source_out, int32_t *far, cudaStream_t s);
+cudaError_t launch_bfs_frontier_deg(int32_t fsize, const int32_t *frontier, const int64_t *row_off, int32_t *fdeg,
+                                    cudaStream_t s);
+// One level: the vertices first reached from the frontier get level + 1 and join next (*nnext counts them).
+cudaError_t launch_bfs_expand(int32_t level, int32_t fsize, const int32_t *frontier, const int64_t *foff,
+                              const int64_t *row_off, const int32_t *col_idx, int32_t *dist, int32_t *next,
+                              int32_t *nnext, cudaStream_t s);
+// *far = min(*far, the lowest id at distance ecc).
+cudaError_t launch_bfs_far(int64_t n, const int32_t *dist, int32_t ecc, int32_t *far, cudaStream_t s);
+
 }  // namespace hrg
