@@ -11,21 +11,16 @@
 #include <algorithm>
 #include <climits>
 #include "hrg_graph_ops.h"
+#include "hrg_graph_util.cuh"
 
 namespace hrg {
 
 namespace {
 
+using namespace graph_util;
+
 constexpr int kThreads = 256;
 constexpr int kEdgesPerThread = 16;
-
-inline unsigned grid_for(int64_t items, int per_block)
-{
-    int64_t g = (items + per_block - 1) / per_block;
-    if (g < 1) g = 1;
-    if (g > (1 << 20)) g = 1 << 20;
-    return (unsigned)g;
-}
 
 __global__ void k_bfs_init(int64_t n, int32_t *__restrict__ dist, const int64_t *__restrict__ row_off,
                            unsigned long long *__restrict__ best)
@@ -65,18 +60,6 @@ __global__ void k_bfs_frontier_deg(int32_t fsize, const int32_t *__restrict__ fr
     }
 }
 
-// the frontier index owning edge e: the last i with foff[i] <= e
-__device__ __forceinline__ int32_t owner(const int64_t *__restrict__ foff, int32_t fsize, int64_t e)
-{
-    int32_t lo = 0, hi = fsize - 1;
-    while (lo < hi) {
-        const int32_t mid = (lo + hi + 1) >> 1;
-        if (foff[mid] <= e) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 __global__ void k_bfs_expand(int32_t level, int32_t fsize, const int32_t *__restrict__ frontier,
                              const int64_t *__restrict__ foff, const int64_t *__restrict__ row_off,
                              const int32_t *__restrict__ col_idx, int32_t *__restrict__ dist,
@@ -86,7 +69,7 @@ __global__ void k_bfs_expand(int32_t level, int32_t fsize, const int32_t *__rest
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * kEdgesPerThread;
     for (int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kEdgesPerThread; e0 < E; e0 += stride) {
         const int64_t e1 = min(e0 + (int64_t)kEdgesPerThread, E);
-        int32_t i = owner(foff, fsize, e0);
+        int32_t i = (int32_t)last_at_most(foff, 0, fsize - 1, e0);  // the frontier vertex of edge e0
         int64_t ib = foff[i], ie = foff[i + 1];
         int32_t u = frontier[i];
         int64_t rb = row_off[u];

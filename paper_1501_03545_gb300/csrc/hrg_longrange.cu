@@ -22,21 +22,16 @@
 #include <algorithm>
 #include "hrg_common.cuh"
 #include "hrg_graph_ops.h"
+#include "hrg_graph_util.cuh"
 
 namespace hrg {
 
 namespace {
 
+using namespace graph_util;
+
 constexpr int kThreads = 256;
 constexpr int kWarpsPerBlock = kThreads / 32;
-
-inline unsigned grid_for(int64_t items, int per_block)
-{
-    int64_t g = (items + per_block - 1) / per_block;
-    if (g < 1) g = 1;
-    if (g > (1 << 20)) g = 1 << 20;
-    return (unsigned)g;
-}
 
 __device__ __forceinline__ void random_pair(int64_t k, uint64_t seed, uint64_t n, int32_t &u, int32_t &v)
 {
@@ -73,13 +68,8 @@ __global__ void k_lr_fill(int64_t n, int64_t count, uint64_t seed, const int64_t
 
 __device__ __forceinline__ bool in_sorted(const int32_t *__restrict__ a, int64_t len, int32_t x)
 {
-    int64_t lo = 0, hi = len;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo < len && a[lo] == x;
+    const int64_t i = lower_bound(a, 0, len, x);
+    return i < len && a[i] == x;
 }
 
 // one thread per vertex: its drawn partners sorted (insertion), repeats and
@@ -111,29 +101,7 @@ __global__ void k_lr_clean(int64_t n, const int64_t *__restrict__ row_off, const
     }
 }
 
-__device__ __forceinline__ int64_t count_below(const int32_t *__restrict__ a, int64_t len, int32_t x)
-{
-    int64_t lo = 0, hi = len;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 constexpr int kRun = 32;  // old entries per lane of the flat merge
-
-// the last v in [lo, hi] with row_off[v] <= q (row_off[lo] <= q assumed)
-__device__ __forceinline__ int64_t row_of(const int64_t *__restrict__ row_off, int64_t lo, int64_t hi, int64_t q)
-{
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (row_off[mid] <= q) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 // old entries at their new places; warp chunk = 32 * kRun entries, lane run = kRun
 __global__ void k_lr_merge_old(int64_t n, const int64_t *__restrict__ row_off, const int32_t *__restrict__ col_idx,
@@ -149,14 +117,14 @@ __global__ void k_lr_merge_old(int64_t n, const int64_t *__restrict__ row_off, c
          c0 += nwarps * chunk) {
         // rows of the chunk's first and last entries, once per warp
         int64_t v_lo = 0, v_hi = 0;
-        if (lane == 0) v_lo = row_of(row_off, 0, n - 1, base + c0);
-        if (lane == 31) v_hi = row_of(row_off, 0, n - 1, base + min(c0 + chunk, total) - 1);
+        if (lane == 0) v_lo = last_at_most(row_off, 0, n - 1, base + c0);
+        if (lane == 31) v_hi = last_at_most(row_off, 0, n - 1, base + min(c0 + chunk, total) - 1);
         v_lo = __shfl_sync(0xffffffffu, v_lo, 0);
         v_hi = __shfl_sync(0xffffffffu, v_hi, 31);
         const int64_t p0 = c0 + (int64_t)lane * kRun;
         if (p0 >= total) continue;
         const int64_t p1 = min(p0 + (int64_t)kRun, total);
-        int64_t v = row_of(row_off, v_lo, v_hi, base + p0);
+        int64_t v = last_at_most(row_off, v_lo, v_hi, base + p0);
         int64_t rb = row_off[v], re = row_off[v + 1];
         for (int64_t p = p0; p < p1; ++p) {
             const int64_t q = base + p;
@@ -167,7 +135,7 @@ __global__ void k_lr_merge_old(int64_t n, const int64_t *__restrict__ row_off, c
             }
             const int32_t x = col_idx[q];
             const int64_t f = fin[v];
-            const int64_t shift = f ? count_below(list + loff[v], f, x) : 0;
+            const int64_t shift = f ? lower_bound(list + loff[v], 0, f, x) : 0;
             col_out[row_off_out[v] + (q - rb) + shift] = x;
         }
     }
@@ -188,7 +156,7 @@ __global__ void k_lr_merge_new(int64_t n, const int64_t *__restrict__ row_off, c
         const int32_t *Nw = list + loff[v];
         for (int64_t j = 0; j < f; ++j) {
             const int32_t y = Nw[j];
-            col_out[row_off_out[v] + j + count_below(O, d, y)] = y;
+            col_out[row_off_out[v] + j + lower_bound(O, 0, d, y)] = y;
         }
     }
 }

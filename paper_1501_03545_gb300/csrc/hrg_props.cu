@@ -20,36 +20,17 @@
 #include <algorithm>
 #include <cstdio>
 #include "hrg_graph_ops.h"
+#include "hrg_graph_util.cuh"
 
 namespace hrg {
 
 namespace {
 
+using namespace graph_util;
+
 constexpr int kThreads = 256;
 constexpr int kWarpsPerBlock = kThreads / 32;
 constexpr int kHistSmem = 2048;  // degrees below this are binned in shared memory first
-
-inline unsigned grid_for(int64_t items, int per_block)
-{
-    int64_t g = (items + per_block - 1) / per_block;
-    if (g < 1) g = 1;
-    if (g > (1 << 20)) g = 1 << 20;
-    return (unsigned)g;
-}
-
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // acc_i: [0] largest degree, [1] tail count, [2] triads; acc_d: [0] tail log sum
 __global__ void k_degree_stats(int64_t n, const int64_t *__restrict__ row_off, int64_t d_min,
@@ -132,16 +113,6 @@ __global__ void k_out_edges(int64_t n, const int64_t *__restrict__ row_off, cons
         }
         if (!FILL && lane == 0) out_deg[v] = cnt;
     }
-}
-
-__device__ __forceinline__ int64_t lower_bound(const int32_t *__restrict__ a, int64_t lo, int64_t hi, int32_t x)
-{
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
 }
 
 // Triangles: warp per u, lane per v in N+(u), |N+(u) ∩ N+(v)| by searching
