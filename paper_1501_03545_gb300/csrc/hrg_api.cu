@@ -141,6 +141,14 @@ static int set_err(hrg_ctx *c, int code, const char *fmt, ...)
                            __FILE__, __LINE__);                                                    \
     } while (0)
 
+// Kept-row buffer of the rim count pass: room for 16 entries per vertex.  The
+// scatter's 32-byte point records use it before the count pass.
+static int64_t small_capacity(int64_t n) { return std::min<int64_t>(16 * n + 1024, 0x7fff0000LL); }
+static size_t small_bytes(int64_t n)
+{
+    return std::max(sizeof(int32_t) * (size_t)small_capacity(n), sizeof(PointRec) * (size_t)n);
+}
+
 static int ensure(hrg_ctx *ctx, int slot, size_t bytes, void **out)
 {
     DevBuf &b = ctx->ws[slot];
@@ -346,8 +354,8 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     // rim rows of up to kKeepRow entries kept by the count pass (room for 16
     // entries per vertex; rows that find none are traversed again)
     void *small = nullptr, *small_off = nullptr, *small_cur = nullptr;
-    const int64_t small_cap = std::min<int64_t>(16 * n + 1024, 0x7fff0000LL);
-    if ((rc = ensure(ctx, hrg_ctx::W_SMALL, sizeof(int32_t) * small_cap, &small))) return rc;
+    const int64_t small_cap = small_capacity(n);
+    if ((rc = ensure(ctx, hrg_ctx::W_SMALL, small_bytes(n), &small))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SMALLOFF, sizeof(int32_t) * n, &small_off))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SMALLCUR, sizeof(unsigned long long), &small_cur))) return rc;
     b.small = (int32_t *)small;
@@ -479,8 +487,10 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
 
     // 2. counting sort by (band, angular bucket)
     CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, p.G, scanws, st));
-    CK(launch_scatter_soa(p, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, J.r, J.phi, (uint64_t *)A,
-                          (PMS *)pms, (PMS64 *)pms64, (int32_t *)pos_of, st));
+    void *recs = nullptr;  // the FP32 path's point records (in the kept-row buffer, idle until the count pass)
+    if (!pms64 && (rc = ensure(ctx, hrg_ctx::W_SMALL, small_bytes(n), &recs))) return rc;
+    CK(launch_scatter_soa(p, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, J.r, J.phi, (PointRec *)recs,
+                          (uint64_t *)A, (PMS *)pms, (PMS64 *)pms64, (int32_t *)pos_of, st));
     CK(cudaEventRecord(ctx->ev[2], st));
     // the exact band counts (read back behind the scan and the scatter): hub
     // queries and empty innermost bands
@@ -687,8 +697,11 @@ extern "C" int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_p
 
     // 2. counting sort by (graph, band, angular bucket); hub query list
     CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, G, scanws, st));
+    void *recs = nullptr;  // the FP32 path's point records (in the kept-row buffer, idle until the count pass)
+    if (!pms64 && (rc = ensure(ctx, hrg_ctx::W_SMALL, small_bytes(N), &recs))) return rc;
     CK(launch_scatter_soa_batch(P, (int32_t *)graph_of, N, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, r_out,
-                                phi_out, (uint64_t *)A, (PMS *)pms, (PMS64 *)pms64, (int32_t *)pos_of, st));
+                                phi_out, (PointRec *)recs, (uint64_t *)A, (PMS *)pms, (PMS64 *)pms64,
+                                (int32_t *)pos_of, st));
     CK(launch_hub_list(P, count, (int32_t *)start, (int32_t *)hub_cnt, (int32_t *)hub_off, nullptr, scanws, st,
                        false));
     int32_t *hh = (int32_t *)ctx->pinned;
@@ -788,10 +801,10 @@ extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
     for (int k = 0; k < 8; ++k) out->stage_ms[k] = job->stage_ms[k];
     // kernels launched: points with their buckets (1; an injected point set:
     // band counts + bucket histogram, 2), bucket scan, structure-of-arrays
-    // scatter (1), count (hub 3, rim 1), row-offset scan, write (hub 3, rim
-    // 1), row sorts (warp 1, CTA 1, big 7)
+    // scatter (records + split, 2; the FP64 path 1), count (hub 3, rim 1),
+    // row-offset scan, write (hub 3, rim 1), row sorts (warp 1, CTA 1, big 7)
     const int64_t n = job->plan.n;
-    const int scatter = 1;
+    const int scatter = job->fp64 ? 1 : 2;
     int L;
     if (job->batch) {
         // graph map, points with their buckets, bucket scan, structure-of-arrays

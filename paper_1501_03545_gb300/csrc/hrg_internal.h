@@ -25,10 +25,14 @@ cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi
                                int32_t *cnt, cudaStream_t s);
 // Structure-of-arrays in bucket order (point i at start[gbuf[i]] + slot[i]):
 // fixed-point angle, FP32 scaled exps + id; optionally the FP64 data of the
-// plain double-precision path.  pos_of[i] receives point i's position.
+// plain double-precision path.  pos_of[i] receives point i's position.  With
+// rec (PointRec[n] scratch) non-null, angle and exps travel as one record per
+// position and a second kernel splits them (FP32 path; pms64 must be null).
+struct __align__(32) PointRec { PMS q; uint64_t A; uint64_t pad; };
+static_assert(sizeof(PointRec) == 32, "one record is one 32-byte sector");
 cudaError_t launch_scatter_soa(const Plan &p, const int32_t *gbuf, const int32_t *slot, const int32_t *start,
-                               const double *r, const double *phi, uint64_t *A, PMS *pms, PMS64 *pms64,
-                               int32_t *pos_of, cudaStream_t s);
+                               const double *r, const double *phi, PointRec *rec, uint64_t *A, PMS *pms,
+                               PMS64 *pms64, int32_t *pos_of, cudaStream_t s);
 
 // Batches: plans[NG] in device memory, graph g owning positions and global
 // ids [plans[g].id_off, plans[g].id_off + plans[g].n).
@@ -37,7 +41,8 @@ cudaError_t launch_sample_bucket_batch(const Plan *plans, const int32_t *graph_o
                                        int32_t *gbuf, int32_t *slot, int32_t *cnt, cudaStream_t s);
 cudaError_t launch_scatter_soa_batch(const Plan *plans, const int32_t *graph_of, int64_t N, const int32_t *gbuf,
                                      const int32_t *slot, const int32_t *start, const double *r, const double *phi,
-                                     uint64_t *A, PMS *pms, PMS64 *pms64, int32_t *pos_of, cudaStream_t s);
+                                     PointRec *rec, uint64_t *A, PMS *pms, PMS64 *pms64, int32_t *pos_of,
+                                     cudaStream_t s);
 // hub queries of every graph: fill=false counts them (hub_cnt[NG]) and scans
 // into hub_off[NG+1]; fill=true writes their positions into hub_pos
 cudaError_t launch_hub_list(const Plan *plans, int NG, const int32_t *start, int32_t *hub_cnt, int32_t *hub_off,

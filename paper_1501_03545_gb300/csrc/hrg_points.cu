@@ -17,6 +17,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kSampleGrid = 152 * 16;  // persistent grid of the samplers (each CTA loads the log table once)
+constexpr int kSplitGrid = 152 * 8;    // persistent: the split reads the records front to back
 
 // 1/F_j and log F_j, F_j = 1 + j/128 (log_table); filled once per device
 __device__ double g_log_tab[256];
@@ -104,29 +105,55 @@ __global__ void k_bucket_hist(Plan p, const double *__restrict__ r, const double
 }
 
 // Structure of arrays in (band, bucket) order, written from id order: point i
-// goes to position start[gbuf[i]] + slot[i], recorded in pos_of[i].
+// goes to position k = start[gbuf[i]] + slot[i], recorded in pos_of[i].  The
+// positions are random, so an 8-byte angle and a 16-byte {P, M, S, id} stored
+// there would each be a partial 32-byte sector, which DRAM reads and writes
+// back.  With rec non-null the two go out as one 32-byte record per position
+// instead (a whole sector), and k_split separates the records sequentially;
+// the plain FP64 path stores its three arrays directly.
 __device__ __forceinline__ void place_point(const Plan &p, int64_t i, const int32_t *__restrict__ gbuf,
                                             const int32_t *__restrict__ slot, const int32_t *__restrict__ start,
                                             const double *__restrict__ r, const double *__restrict__ phi,
-                                            uint64_t *__restrict__ A, PMS *__restrict__ pms,
-                                            PMS64 *__restrict__ pms64, int32_t *__restrict__ pos_of)
+                                            PointRec *__restrict__ rec, uint64_t *__restrict__ A,
+                                            PMS *__restrict__ pms, PMS64 *__restrict__ pms64,
+                                            int32_t *__restrict__ pos_of)
 {
     const int64_t k = (int64_t)__ldg(start + gbuf[i]) + slot[i];
     pos_of[i] = (int32_t)k;
     const double rr = r[i], ph = phi[i];
-    A[k] = angle_key(ph);
-    pms[k] = scaled_exps(p, rr, (int32_t)i);
-    if (pms64) pms64[k] = scaled_exps64(p, rr, ph);
+    const PMS q = scaled_exps(p, rr, (int32_t)i);
+    const uint64_t a = angle_key(ph);
+    if (rec) {
+        int4 *dst = reinterpret_cast<int4 *>(rec + k);
+        dst[0] = *reinterpret_cast<const int4 *>(&q);
+        dst[1] = make_int4((int)(uint32_t)a, (int)(uint32_t)(a >> 32), 0, 0);
+    } else {
+        A[k] = a;
+        pms[k] = q;
+        if (pms64) pms64[k] = scaled_exps64(p, rr, ph);
+    }
 }
 
 __global__ void k_scatter_soa(Plan p, const int32_t *__restrict__ gbuf, const int32_t *__restrict__ slot,
                               const int32_t *__restrict__ start, const double *__restrict__ r,
-                              const double *__restrict__ phi, uint64_t *__restrict__ A, PMS *__restrict__ pms,
-                              PMS64 *__restrict__ pms64, int32_t *__restrict__ pos_of)
+                              const double *__restrict__ phi, PointRec *__restrict__ rec, uint64_t *__restrict__ A,
+                              PMS *__restrict__ pms, PMS64 *__restrict__ pms64, int32_t *__restrict__ pos_of)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride)
-        place_point(p, i, gbuf, slot, start, r, phi, A, pms, pms64, pos_of);
+        place_point(p, i, gbuf, slot, start, r, phi, rec, A, pms, pms64, pos_of);
+}
+
+// the records, in position order, into the angle and {P, M, S, id} arrays
+__global__ void k_split(int64_t N, const PointRec *__restrict__ rec, uint64_t *__restrict__ A, PMS *__restrict__ pms)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
+        const int4 *src = reinterpret_cast<const int4 *>(rec + k);
+        const int4 lo = __ldcs(src), hi = __ldcs(src + 1);
+        reinterpret_cast<int4 *>(pms)[k] = lo;
+        A[k] = ((uint64_t)(uint32_t)hi.y << 32) | (uint32_t)hi.x;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -167,12 +194,13 @@ __global__ void k_sample_bucket_batch(const Plan *__restrict__ plans, const int3
 __global__ void k_scatter_soa_batch(const Plan *__restrict__ plans, const int32_t *__restrict__ graph_of, int64_t N,
                                     const int32_t *__restrict__ gbuf, const int32_t *__restrict__ slot,
                                     const int32_t *__restrict__ start, const double *__restrict__ r,
-                                    const double *__restrict__ phi, uint64_t *__restrict__ A, PMS *__restrict__ pms,
-                                    PMS64 *__restrict__ pms64, int32_t *__restrict__ pos_of)
+                                    const double *__restrict__ phi, PointRec *__restrict__ rec,
+                                    uint64_t *__restrict__ A, PMS *__restrict__ pms, PMS64 *__restrict__ pms64,
+                                    int32_t *__restrict__ pos_of)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
-        place_point(plans[__ldg(graph_of + i)], i, gbuf, slot, start, r, phi, A, pms, pms64, pos_of);
+        place_point(plans[__ldg(graph_of + i)], i, gbuf, slot, start, r, phi, rec, A, pms, pms64, pos_of);
 }
 
 // hub queries of graph g: its positions before its first rim-band bucket
@@ -347,11 +375,12 @@ cudaError_t launch_bucket_hist(const Plan &p, const double *r, const double *phi
 }
 
 cudaError_t launch_scatter_soa(const Plan &p, const int32_t *gbuf, const int32_t *slot, const int32_t *start,
-                               const double *r, const double *phi, uint64_t *A, PMS *pms, PMS64 *pms64,
-                               int32_t *pos_of, cudaStream_t s)
+                               const double *r, const double *phi, PointRec *rec, uint64_t *A, PMS *pms,
+                               PMS64 *pms64, int32_t *pos_of, cudaStream_t s)
 {
-    k_scatter_soa<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, gbuf, slot, start, r, phi, A, pms, pms64,
+    k_scatter_soa<<<grid_for(p.n, kThreads, 4), kThreads, 0, s>>>(p, gbuf, slot, start, r, phi, rec, A, pms, pms64,
                                                                    pos_of);
+    if (rec) k_split<<<std::min(grid_for(p.n, kThreads, 4), kSplitGrid), kThreads, 0, s>>>(p.n, rec, A, pms);
     return cudaGetLastError();
 }
 
@@ -382,10 +411,12 @@ cudaError_t launch_sample_bucket_batch(const Plan *plans, const int32_t *graph_o
 
 cudaError_t launch_scatter_soa_batch(const Plan *plans, const int32_t *graph_of, int64_t N, const int32_t *gbuf,
                                      const int32_t *slot, const int32_t *start, const double *r, const double *phi,
-                                     uint64_t *A, PMS *pms, PMS64 *pms64, int32_t *pos_of, cudaStream_t s)
+                                     PointRec *rec, uint64_t *A, PMS *pms, PMS64 *pms64, int32_t *pos_of,
+                                     cudaStream_t s)
 {
     k_scatter_soa_batch<<<grid_for(N, kThreads, 4), kThreads, 0, s>>>(plans, graph_of, N, gbuf, slot, start, r, phi,
-                                                                       A, pms, pms64, pos_of);
+                                                                       rec, A, pms, pms64, pos_of);
+    if (rec) k_split<<<std::min(grid_for(N, kThreads, 4), kSplitGrid), kThreads, 0, s>>>(N, rec, A, pms);
     return cudaGetLastError();
 }
 
