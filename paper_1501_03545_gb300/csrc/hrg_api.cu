@@ -86,6 +86,8 @@ struct hrg_job {
     Plan plan{};
     bool fp64 = false;
     bool sampled = false;  // points drawn by the generator (else injected)
+    bool hub_pooled = false;  // the count pass kept every hub entry: the write pass copies them
+    int32_t hub_runs = 0;
     bool open = false;
     bool finished = false;
     int32_t p_hub = 0;
@@ -111,7 +113,7 @@ struct hrg_ctx {
            W_HEAVY, W_CURSOR, W_SMALL, W_SMALLOFF, W_SMALLCUR, W_PLANS, W_NOFF, W_SOFF, W_GRAPHOF, W_HUBCNT,
            W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_POSOF, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
            W_PACC, W_POUTDEG, W_POUTOFF, W_POUTCOL, W_PTRI, W_PSCAN, W_LRCNT, W_LROFF, W_LRLIST, W_LRFIN,
-           W_LRDEG, W_BFSF0, W_BFSF1, W_BFSDEG, W_BFSOFF, W_BFSACC, W_BFSDIST,
+           W_LRDEG, W_HPOOL, W_HRUNS, W_HPCUR, W_BFSF0, W_BFSF1, W_BFSDEG, W_BFSOFF, W_BFSACC, W_BFSDIST,
            W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
@@ -363,6 +365,14 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     b.small_cursor = (unsigned long long *)small_cur;
     b.small_cap = small_cap;
 
+    // the hub rows' ids, kept by the count pass in runs (room for 8 per vertex:
+    // on overflow the write pass traverses the hub rows again instead)
+    void *pool = nullptr, *runs = nullptr, *pool_cur = nullptr;
+    const int64_t pool_cap = 8 * n + (1 << 24);
+    if (J.p_hub > 0) {
+        if ((rc = ensure(ctx, hrg_ctx::W_HPOOL, sizeof(int32_t) * pool_cap, &pool))) return rc;
+        if ((rc = ensure(ctx, hrg_ctx::W_HPCUR, sizeof(unsigned long long), &pool_cur))) return rc;
+    }
     char *hp = (char *)ctx->pinned;
     for (int attempt = 0;; ++attempt) {
         if ((rc = ensure(ctx, hrg_ctx::W_HEAVY, sizeof(int4) * heavy_cap, &heavy))) return rc;
@@ -370,6 +380,17 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
         b.heavy = (int4 *)heavy;
         b.seg_cnt = (int32_t *)scnt;
         b.heavy_cap = (int32_t)heavy_cap;
+        // a warp's runs hold at least 1024 - 64 ids, except its last one and one per heavy chunk
+        const int64_t run_cap = std::min<int64_t>(pool_cap / 512 + J.p_hub + heavy_cap + 1024, (1 << 24) - 1);
+        if (J.p_hub > 0) {
+            if ((rc = ensure(ctx, hrg_ctx::W_HRUNS, sizeof(int4) * run_cap, &runs))) return rc;
+            CK(cudaMemsetAsync(pool_cur, 0, sizeof(unsigned long long), st));
+        }
+        b.pool = (int32_t *)pool;
+        b.runs = (int4 *)runs;
+        b.pool_cur = (unsigned long long *)pool_cur;
+        b.pool_cap = pool_cap;
+        b.run_cap = (int32_t)run_cap;
         CK(cudaMemsetAsync(stats, 0, sizeof(uint64_t) * 8, st));
         CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 16, st));
         CK(cudaMemsetAsync(bigtot, 0, sizeof(int64_t), st));
@@ -389,7 +410,17 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
         CK(cudaMemcpyAsync(hp + 8, listcnt, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(hp + 24, bigtot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(hp + 64, stats, sizeof(uint64_t) * 8, cudaMemcpyDeviceToHost, st));
+        if (pool_cur) CK(cudaMemcpyAsync(hp + 128, pool_cur, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        J.hub_pooled = false;
+        J.hub_runs = 0;
+        if (pool_cur) {
+            uint64_t pc;
+            memcpy(&pc, hp + 128, 8);
+            const uint64_t entries = pc & ((1ull << 40) - 1), nruns = pc >> 40;
+            J.hub_pooled = entries <= (uint64_t)pool_cap && nruns <= (uint64_t)b.run_cap;
+            J.hub_runs = J.hub_pooled ? (int32_t)nruns : 0;
+        }
         int32_t heavy_found;
         memcpy(&heavy_found, hp + 8 + 12, 4);
         if (J.p_hub == 0 || heavy_found <= heavy_cap) break;
@@ -750,7 +781,10 @@ extern "C" int hrg_generate_finish(hrg_job *job, int32_t *col_idx_out)
     const Plan &p = job->plan;
     CK(cudaEventRecord(ctx->ev[6], st));
     if (job->p_hub > 0) CK(cudaMemsetAsync(job->qb.cursor, 0, sizeof(int32_t) * job->p_hub, st));
-    CK(launch_write_hub(p, job->qb, job->fp64, job->p_hub, job->row_off, col_idx_out, st));
+    if (job->hub_pooled)
+        CK(launch_copy_hub(job->qb, job->p_hub, job->hub_runs, job->row_off, col_idx_out, st));
+    else
+        CK(launch_write_hub(p, job->qb, job->fp64, job->p_hub, job->row_off, col_idx_out, st));
     CK(cudaEventRecord(ctx->ev[7], st));
     CK(launch_write_rim(p, job->qb, job->fp64, job->row_off, col_idx_out, st));
     CK(cudaEventRecord(ctx->ev[8], st));
@@ -811,14 +845,19 @@ extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
         // scatter, hub count + scan (+ fill), count, row-offset scan
         L = 1 + 1 + scan_launches(job->batch_G) + scatter + 1 + scan_launches(job->batch) +
             (job->p_hub > 0 ? 1 : 0) + (job->p_hub > 0 ? 3 : 0) + (job->qb.n_sectors > 0 ? 1 : 0) + scan_launches(n);
-        if (job->finished) L += (job->p_hub > 0 ? 3 : 0) + (job->qb.n_sectors > 0 ? 1 : 0) + sort_launches(job->lists);
+        if (job->finished)
+            L += (job->p_hub > 0 ? (job->hub_pooled ? (job->hub_runs > 0 ? 2 : 1) : 3) : 0) +
+                 (job->qb.n_sectors > 0 ? 2 : 0) + sort_launches(job->lists);
         out->launches = L;
         out->buckets = job->batch_G;
         return HRG_OK;
     }
     L = (job->sampled ? 1 : 2) + scan_launches(job->plan.G) + scatter + query_launches(job->plan, job->p_hub, false) +
         scan_launches(n);
-    if (job->finished) L += query_launches(job->plan, job->p_hub, true) + sort_launches(job->lists);
+    if (job->finished) {
+        L += query_launches(job->plan, job->p_hub, true) + sort_launches(job->lists);
+        if (job->p_hub > 0 && job->hub_pooled) L -= job->hub_runs > 0 ? 1 : 2;  // copy + check instead of 3
+    }
     out->launches = L;
     return HRG_OK;
 }

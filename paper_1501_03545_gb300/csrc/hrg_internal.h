@@ -108,6 +108,12 @@ struct QueryBufs {
     int32_t *warp_cnt;        // [p_hub] entries a hub query's own warp found (count pass)
     int32_t *seg_cnt;         // [heavy_cap] entries found in each heavy segment (count pass)
     int32_t *col_out;         // CSR neighbour ids being written (write pass only)
+    // hub entries pooled by the count pass (null pool: not pooled)
+    int32_t *pool;            // [pool_cap] the ids found for hub rows, in runs of one query each
+    int4 *runs;               // [run_cap] (hub query, entries, pool offset lo, hi) of every run
+    unsigned long long *pool_cur;  // [1] runs reserved << 40 | pool entries reserved (above the caps: overflow)
+    int64_t pool_cap;         // below 2^40
+    int32_t run_cap;          // below 2^24
     int32_t *small;           // [small_cap] rim rows of up to kKeepRow entries kept by the count pass
     int32_t *small_off;       // [n] by position: start of the kept row in small, -1 if none
     unsigned long long *small_cursor;  // [1] bump allocator over small
@@ -132,6 +138,10 @@ cudaError_t launch_count_rim(const Plan &p, const QueryBufs &b, bool fp64_only, 
 // Same traversals, writing neighbour ids into col_idx[row_off[id] ..]; hub
 // rows are written in no particular order (sorted later): the query's warp
 // first, then its heavy segments, each at an offset reserved with one atomic.
+// The hub rows from the pooled runs (one atomic per run on the row's cursor,
+// cursor zeroed by the caller), then the cursors checked against the degrees.
+cudaError_t launch_copy_hub(const QueryBufs &b, int32_t p_hub, int32_t n_runs, const int64_t *row_off,
+                            int32_t *col_idx, cudaStream_t s);
 cudaError_t launch_write_hub(const Plan &p, const QueryBufs &b, bool fp64_only, int32_t p_hub,
                              const int64_t *row_off, int32_t *col_idx, cudaStream_t s);
 // Rim rows: kept rows are sorted and copied, the others traversed again.

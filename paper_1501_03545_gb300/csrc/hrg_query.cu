@@ -466,8 +466,41 @@ __global__ void __launch_bounds__(256, 4) k_rim_sector(Plan p, QueryBufs b)
 // Ranges longer than kHeavy are cut into chunks (count pass) and processed by
 // whole CTAs (k_hub_heavy), so no single warp walks millions of candidates.
 // Degrees accumulate with atomics; rows are written through a per-row cursor
-// in no particular order and sorted afterwards.
+// in no particular order and sorted afterwards.  The count pass also keeps
+// the ids it finds: a warp gathers them in shared memory (kHubStage) and, when
+// that fills, reserves a run of the global pool with one atomic and copies
+// them there, tagged with the query; a heavy chunk flushes its (at most
+// kHeavy) ids once.  The write pass then copies the runs into the rows
+// (k_hub_copy) instead of deciding the candidates again; only when the pool
+// overflowed does it traverse them again.
 // ---------------------------------------------------------------------------
+constexpr int kHubStage = 1024;
+constexpr int kPoolRunShift = 40;  // pool_cur[0] = runs << 40 | entries: one atomic reserves both
+
+// a run of `fill` ids: (pool offset, run index), or false when the pool or
+// the run table overflowed (the host then traverses the hub rows again)
+__device__ __forceinline__ bool pool_reserve(const QueryBufs &b, int32_t fill, unsigned long long &off,
+                                             unsigned long long &run)
+{
+    const unsigned long long old = atomicAdd(&b.pool_cur[0], (1ull << kPoolRunShift) | (unsigned long long)fill);
+    off = old & ((1ull << kPoolRunShift) - 1);
+    run = old >> kPoolRunShift;
+    return off + (unsigned long long)fill <= (unsigned long long)b.pool_cap && run < (unsigned long long)b.run_cap;
+}
+
+// ids buf[0, fill) of hub query qi into a run of the pool (whole warp)
+__device__ __forceinline__ void pool_flush(const QueryBufs &b, int32_t qi, const int32_t *buf, int32_t fill, int lane)
+{
+    if (fill == 0) return;
+    unsigned long long off = 0, run = 0;
+    int ok = 0;
+    if (lane == 0) ok = pool_reserve(b, fill, off, run);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return;
+    off = __shfl_sync(0xffffffffu, off, 0);
+    for (int32_t k = lane; k < fill; k += 32) b.pool[off + k] = buf[k];
+    if (lane == 0) b.runs[run] = make_int4(qi, fill, (int)(uint32_t)off, (int)(uint32_t)(off >> 32));
+}
 __device__ __forceinline__ Ranges shfl_ranges(const Ranges &r, int src)
 {
     Ranges o;
@@ -496,7 +529,7 @@ __device__ __forceinline__ void warp_put(int32_t *__restrict__ out, int64_t base
 // list of a batch maps one to the other).
 template <bool F64, bool WRITE>
 __device__ __forceinline__ void hub_query(const Plan &p, const QueryBufs &b, int32_t qi, int32_t qp,
-                                          const int64_t *__restrict__ row_off)
+                                          const int64_t *__restrict__ row_off, int32_t *stage)
 {
     const int lane = threadIdx.x & 31;
     const PMS q = b.pms[qp];
@@ -517,6 +550,8 @@ __device__ __forceinline__ void hub_query(const Plan &p, const QueryBufs &b, int
     int32_t mine = 0;
     int32_t pos = 0;                               // write pass: entries this warp has written
     const int32_t lim = WRITE ? b.warp_cnt[qi] : 0;  // ... and must write
+    const bool pooled = !WRITE && b.pool != nullptr;
+    int32_t fill = 0;                              // count pass: ids gathered in stage (warp-uniform)
     for (int j = 0; j < p.B; ++j) {
         const Ranges rg = shfl_ranges(j < 32 ? rA : rB, j & 31);
         for (int part = 0; part < 2; ++part) {
@@ -546,11 +581,28 @@ __device__ __forceinline__ void hub_query(const Plan &p, const QueryBufs &b, int
                     warp_put(b.col_out, base, lim, pos, eb, pb.id - p.id_off, lt);
                 } else {
                     mine += (int)ea + (int)eb;
+                    if (pooled) {
+                        const unsigned ma = __ballot_sync(0xffffffffu, ea), mb = __ballot_sync(0xffffffffu, eb);
+                        const int32_t add = __popc(ma) + __popc(mb);
+                        if (fill + add > kHubStage) {
+                            __syncwarp();
+                            pool_flush(b, qi, stage, fill, lane);
+                            __syncwarp();
+                            fill = 0;
+                        }
+                        if (ea) stage[fill + __popc(ma & lt)] = pa.id - p.id_off;
+                        if (eb) stage[fill + __popc(ma) + __popc(mb & lt)] = pb.id - p.id_off;
+                        fill += add;
+                    }
                 }
             }
         }
     }
     if (!WRITE) {
+        if (pooled) {
+            __syncwarp();
+            pool_flush(b, qi, stage, fill, lane);
+        }
         int32_t d = mine;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
@@ -569,13 +621,15 @@ template <bool F64, bool WRITE, bool BATCH>
 __global__ void __launch_bounds__(256) k_hub_warp(Plan p, QueryBufs b, int32_t p_hub,
                                                   const int64_t *__restrict__ row_off)
 {
+    __shared__ int32_t s_stage[WRITE ? 1 : 8][WRITE ? 1 : kHubStage];  // count pass: one stage per warp
     const int32_t qi = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (qi >= p_hub) return;  // uniform per warp
+    int32_t *stage = WRITE ? nullptr : s_stage[WRITE ? 0 : (threadIdx.x >> 5)];
     if (BATCH) {
         const int32_t qp = __ldg(b.hub_pos + qi);
-        hub_query<F64, WRITE>(b.plans[__ldg(b.graph_of + qp)], b, qi, qp, row_off);
+        hub_query<F64, WRITE>(b.plans[__ldg(b.graph_of + qp)], b, qi, qp, row_off, stage);
     } else {
-        hub_query<F64, WRITE>(p, b, qi, qi, row_off);
+        hub_query<F64, WRITE>(p, b, qi, qi, row_off, stage);
     }
 }
 
@@ -584,8 +638,8 @@ __global__ void __launch_bounds__(256) k_hub_warp(Plan p, QueryBufs b, int32_t p
 // many entries of the row with one atomic and places them by warp.
 template <bool F64, bool WRITE>
 __device__ __forceinline__ void heavy_chunk(const Plan &p, const QueryBufs &b, int32_t k, const int4 sg, int32_t qp,
-                                            const int64_t *__restrict__ row_off, int32_t *s_red, unsigned &n_cand,
-                                            unsigned &n_re, unsigned &n_edge)
+                                            const int64_t *__restrict__ row_off, int32_t *s_red, int32_t *s_ids,
+                                            unsigned &n_cand, unsigned &n_re, unsigned &n_edge)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -611,6 +665,11 @@ __device__ __forceinline__ void heavy_chunk(const Plan &p, const QueryBufs &b, i
         lim = s_red[2];
     }
     int32_t mine = 0;
+    const bool pooled = !WRITE && b.pool != nullptr;
+    if (pooled) {  // s_red[8]: ids gathered in s_ids (at most kHeavy: one per candidate)
+        if (threadIdx.x == 0) s_red[8] = 0;
+        __syncthreads();
+    }
     for (int32_t c0 = sg.z; c0 < sg.w; c0 += blockDim.x) {  // uniform trip count per warp
         const int32_t c = c0 + threadIdx.x;
         const bool v = c < sg.w && c != qp;
@@ -618,6 +677,15 @@ __device__ __forceinline__ void heavy_chunk(const Plan &p, const QueryBufs &b, i
         PMS pc{};
         if (v) { Ac = __ldg(b.A + c); pc = b.pms[c]; }
         const bool e = v && decide_loaded<F64>(p, b, q, q64, Aq, Ac, pc, c, W, n_cand, n_re);
+        if (pooled) {
+            const unsigned m = __ballot_sync(0xffffffffu, e);
+            if (m) {
+                int32_t off = 0;
+                if (lane == 0) off = atomicAdd(&s_red[8], __popc(m));
+                off = __shfl_sync(0xffffffffu, off, 0) + __popc(m & lt);
+                if (e) s_ids[off] = pc.id - p.id_off;
+            }
+        }
         if (WRITE) {
             const unsigned m = __ballot_sync(0xffffffffu, e);
             if (m) {
@@ -642,6 +710,24 @@ __device__ __forceinline__ void heavy_chunk(const Plan &p, const QueryBufs &b, i
             b.seg_cnt[k] = t;
             if (t) atomicAdd(&b.deg[q.id], t);
             n_edge += t;
+            // the chunk's ids: one run of the pool (s_red[9..11]: offset lo, hi, keep)
+            const int32_t fill = pooled ? s_red[8] : 0;
+            s_red[11] = 0;
+            if (fill > 0) {
+                unsigned long long off, run;
+                if (pool_reserve(b, fill, off, run)) {
+                    b.runs[run] = make_int4(qi, fill, (int)(uint32_t)off, (int)(uint32_t)(off >> 32));
+                    s_red[9] = (int32_t)(uint32_t)off;
+                    s_red[10] = (int32_t)(uint32_t)(off >> 32);
+                    s_red[11] = fill;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_red[11] > 0) {
+            const unsigned long long off =
+                ((unsigned long long)(uint32_t)s_red[10] << 32) | (unsigned long long)(uint32_t)s_red[9];
+            for (int32_t t = threadIdx.x; t < s_red[11]; t += blockDim.x) b.pool[off + t] = s_ids[t];
         }
         __syncthreads();
     } else {
@@ -655,17 +741,18 @@ __device__ __forceinline__ void heavy_chunk(const Plan &p, const QueryBufs &b, i
 template <bool F64, bool WRITE, bool BATCH>
 __global__ void __launch_bounds__(256) k_hub_heavy(Plan p, QueryBufs b, const int64_t *__restrict__ row_off)
 {
-    __shared__ int32_t s_red[8];
+    __shared__ int32_t s_red[12];
+    __shared__ int32_t s_ids[WRITE ? 1 : kHeavy];  // count pass: the chunk's ids for the pool
     const int32_t nseg = min(*((volatile int32_t *)&b.list_cnt[3]), b.heavy_cap);
     unsigned n_cand = 0, n_re = 0, n_edge = 0;
     for (int32_t k = blockIdx.x; k < nseg; k += gridDim.x) {
         const int4 sg = b.heavy[k];
         if (BATCH) {
             const int32_t qp = __ldg(b.hub_pos + sg.x);
-            heavy_chunk<F64, WRITE>(b.plans[__ldg(b.graph_of + qp)], b, k, sg, qp, row_off, s_red, n_cand, n_re,
-                                    n_edge);
+            heavy_chunk<F64, WRITE>(b.plans[__ldg(b.graph_of + qp)], b, k, sg, qp, row_off, s_red, s_ids, n_cand,
+                                    n_re, n_edge);
         } else {
-            heavy_chunk<F64, WRITE>(p, b, k, sg, sg.x, row_off, s_red, n_cand, n_re, n_edge);
+            heavy_chunk<F64, WRITE>(p, b, k, sg, sg.x, row_off, s_red, s_ids, n_cand, n_re, n_edge);
         }
     }
     if (!WRITE) add_stats(b.stats, n_cand, n_re, n_edge);
@@ -695,6 +782,36 @@ __global__ void k_hub_check(QueryBufs b, int32_t p_hub)
     const int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (qi >= p_hub) return;
     if (b.warp_cnt[qi] + b.cursor[qi] != b.deg[b.pms[hub_position(b, (int32_t)qi)].id])
+        atomicOr((unsigned long long *)&b.stats[ST_ERR], 1ull);
+}
+
+// Write pass from the pool: one warp per run; its place in the row comes from
+// one atomic on the row's cursor.
+__global__ void __launch_bounds__(256) k_hub_copy(QueryBufs b, int32_t n_runs, const int64_t *__restrict__ row_off,
+                                                  int32_t *__restrict__ col_out)
+{
+    const int lane = threadIdx.x & 31;
+    const int32_t nwarps = (int32_t)(gridDim.x * (blockDim.x >> 5));
+    for (int32_t k = (int32_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); k < n_runs; k += nwarps) {
+        const int4 run = b.runs[k];
+        const int32_t qi = run.x, cnt = run.y;
+        const unsigned long long off = ((unsigned long long)(uint32_t)run.w << 32) | (unsigned long long)(uint32_t)run.z;
+        int64_t dst = 0;
+        if (lane == 0) {
+            const int32_t id = b.pms[hub_position(b, qi)].id;
+            dst = row_off[id] + atomicAdd(&b.cursor[qi], cnt);
+        }
+        dst = __shfl_sync(0xffffffffu, dst, 0);
+        for (int32_t t = lane; t < cnt; t += 32) col_out[dst + t] = b.pool[off + t];
+    }
+}
+
+// every pooled hub row complete: its cursor equals its degree
+__global__ void k_hub_check_pooled(QueryBufs b, int32_t p_hub)
+{
+    const int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (qi >= p_hub) return;
+    if (b.cursor[qi] != b.deg[b.pms[hub_position(b, (int32_t)qi)].id])
         atomicOr((unsigned long long *)&b.stats[ST_ERR], 1ull);
 }
 
@@ -764,6 +881,15 @@ cudaError_t launch_count_hub(const Plan &p, const QueryBufs &b, bool fp64_only, 
     if (p_hub <= 0) return cudaSuccess;
     hub_dispatch<false>(p, b, fp64_only, p_hub, nullptr, s);
     k_hub_classify<<<(unsigned)((p_hub + 255) / 256), 256, 0, s>>>(b, p_hub);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_hub(const QueryBufs &b, int32_t p_hub, int32_t n_runs, const int64_t *row_off,
+                            int32_t *col_idx, cudaStream_t s)
+{
+    if (p_hub <= 0) return cudaSuccess;
+    if (n_runs > 0) k_hub_copy<<<kRimWriteGrid / 2, 256, 0, s>>>(b, n_runs, row_off, col_idx);
+    k_hub_check_pooled<<<(unsigned)((p_hub + 255) / 256), 256, 0, s>>>(b, p_hub);
     return cudaGetLastError();
 }
 

@@ -96,12 +96,13 @@ int fail(hrg_server *s, int code, const char *fmt, ...)
 
 // Device bytes of a request: outputs (r, phi, row offsets, neighbour ids at
 // 1.1 kbar per vertex) and the transient workspace of its generation (about
-// 160 bytes per vertex plus the big-row sort buffer).
+// 200 bytes per vertex, the hub-entry pool included, plus the big-row sort
+// buffer).
 void estimate(const hrg_params &p, size_t &out, size_t &work)
 {
     const double n = (double)p.n, e = 1.1 * p.avg_degree * n + 1024.0;
     out = (size_t)(16.0 * n + 8.0 * (n + 1) + 4.0 * e) + 4096;
-    work = (size_t)(160.0 * n + 4.0 * e);
+    work = (size_t)(200.0 * n + 4.0 * e) + ((size_t)1 << 26);
 }
 
 void run_batch(hrg_server *s, hrg_ctx *ctx, cudaStream_t st, std::vector<Req *> &batch)
