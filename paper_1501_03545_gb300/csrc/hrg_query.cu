@@ -8,9 +8,11 @@
 //   * an FP32 test of the scaled predicate with an undecided band of
 //     relative half-width mu, and an FP64 recheck of the pairs inside it, or
 //   * the FP64 predicate on every candidate (the plain double path).
-// The same traversal runs twice: once to count degrees, once to write the
-// neighbour ids into the caller's CSR (rows longer than kRegRow are sorted
-// afterwards by hrg_sort.cu).
+// The count pass counts degrees and keeps what it finds where that is cheap:
+// rim rows of up to kKeepRow ids in a row buffer, hub rows in a pool of runs.
+// The write pass copies those into the caller's CSR and traverses only the
+// longer rim rows again (and the hub rows if the pool overflowed); rows not
+// sorted on the way are sorted afterwards by hrg_sort.cu.
 //
 // Two work mappings:
 //   * rim bands (most vertices, small windows): one CTA per angular sector,
