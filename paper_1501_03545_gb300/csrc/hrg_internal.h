@@ -57,7 +57,6 @@ cudaError_t scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t N, void *ws
 // ---- queries (hrg_query.cu) and row sorts (hrg_sort.cu) ----
 constexpr int kRegRow = 32;       // rows up to this are sorted in registers by the write pass
 constexpr int kKeepRow = 128;     // rows up to this are kept by the count pass (no second traversal)
-constexpr int kCopySortRow = 64;  // kept rows up to this are sorted by the copy, longer ones by the row sort
 constexpr int kWarpRow = 1024;    // rows up to this: one warp, bucket sort in shared memory
 constexpr int kSmemRow = 12288;   // rows up to this: one CTA, bucket sort in shared memory
 
@@ -82,6 +81,38 @@ __device__ __forceinline__ void warp_bitonic64(int32_t &a, int32_t &b, int lane)
                 const bool up_a = (lane & k) == 0, up_b = ((lane + 32) & k) == 0;
                 a = (lower == up_a) ? min(a, pa) : max(a, pa);
                 b = (lower == up_b) ? min(b, pb) : max(b, pb);
+            }
+        }
+    }
+}
+
+// Up to 128 ids sorted the same way with four registers a lane: element
+// i = lane + 32 r in v[r].  Partners 32 or 64 apart sit inside a lane
+// (registers r and r | j/32), nearer ones are exchanged by shuffles.
+__device__ __forceinline__ void warp_bitonic128(int32_t (&v)[4], int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 128; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int rj = j >> 5;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    if (r & rj) continue;  // r is the lower index of the pair (r, r | rj)
+                    const bool up = ((lane + 32 * r) & k) == 0;
+                    const int32_t lo = min(v[r], v[r | rj]), hi = max(v[r], v[r | rj]);
+                    v[r] = up ? lo : hi;
+                    v[r | rj] = up ? hi : lo;
+                }
+            } else {
+                const bool lower = (lane & j) == 0;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int32_t p = __shfl_xor_sync(0xffffffffu, v[r], j);
+                    const bool up = ((lane + 32 * r) & k) == 0;
+                    v[r] = (lower == up) ? min(v[r], p) : max(v[r], p);
+                }
             }
         }
     }
