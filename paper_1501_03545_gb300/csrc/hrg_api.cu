@@ -143,9 +143,9 @@ static int set_err(hrg_ctx *c, int code, const char *fmt, ...)
                            __FILE__, __LINE__);                                                    \
     } while (0)
 
-// Kept-row buffer of the rim count pass: room for 24 entries per vertex.  The
+// Kept-row buffer of the rim count pass: room for 32 entries per vertex.  The
 // scatter's 32-byte point records use it before the count pass.
-static int64_t small_capacity(int64_t n) { return std::min<int64_t>(24 * n + 1024, 0x7fff0000LL); }
+static int64_t small_capacity(int64_t n) { return std::min<int64_t>(32 * n + 1024, 0x7fff0000LL); }
 static size_t small_bytes(int64_t n)
 {
     return std::max(sizeof(int32_t) * (size_t)small_capacity(n), sizeof(PointRec) * (size_t)n);
@@ -353,7 +353,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     }
     b.cursor = (int32_t *)cursor;
     b.warp_cnt = (int32_t *)wcnt;
-    // rim rows of up to kKeepRow entries kept by the count pass (room for 24
+    // rim rows of up to kKeepRow entries kept by the count pass (room for 32
     // entries per vertex, below 2^31 in all; rows that find none are
     // traversed again)
     void *small = nullptr, *small_off = nullptr, *small_cur = nullptr;

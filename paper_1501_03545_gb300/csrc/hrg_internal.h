@@ -56,7 +56,8 @@ cudaError_t scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t N, void *ws
 
 // ---- queries (hrg_query.cu) and row sorts (hrg_sort.cu) ----
 constexpr int kRegRow = 32;       // rows up to this are sorted in registers by the write pass
-constexpr int kKeepRow = 128;     // rows up to this are kept by the count pass (no second traversal)
+constexpr int kKeepRow = 256;     // rows up to this are kept by the count pass (no second traversal)
+constexpr int kCopySortRow = 128; // kept rows up to this are sorted by the copy, longer ones by the row sort
 constexpr int kWarpRow = 1024;    // rows up to this: one warp, bucket sort in shared memory
 constexpr int kSmemRow = 12288;   // rows up to this: one CTA, bucket sort in shared memory
 

@@ -152,10 +152,12 @@ __device__ __forceinline__ void warp_append(int32_t *list, int32_t *count, bool 
 // ---------------------------------------------------------------------------
 // One query, one thread (rim bands).  The count pass stores a row of up to
 // kKeepRow entries in the row buffer (b.small) and records where
-// (b.small_off[position]); the write pass then sorts and copies it instead of
-// traversing the query again (k_rim_copy).  Longer rows, and rows that did
-// not fit in the buffer, are traversed again by the write pass, which keeps
-// rows of up to kRegRow entries sorted in registers.
+// (b.small_off[position]); the write pass then copies it instead of
+// traversing the query again (k_rim_copy), sorting rows of up to
+// kCopySortRow entries on the way (longer kept rows go to the row sort).
+// Longer rows, and rows that did not fit in the buffer, are traversed again
+// by the write pass, which keeps rows of up to kRegRow entries sorted in
+// registers.
 // ---------------------------------------------------------------------------
 // The traversal.  Count pass: every query of the sector; write pass: only
 // queries whose row was not kept (no warp-collective operations there, so
@@ -251,7 +253,7 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
             }
             b.small_off[qp] = off;
             b.deg[q.id] = cnt;
-            if (off < 0) classify_row(b, q.id, cnt);  // kept rows are sorted by k_rim_copy
+            if (off < 0 || cnt > kCopySortRow) classify_row(b, q.id, cnt);  // the rest is sorted by k_rim_copy
         }
         // the write pass's work list: rows to traverse again, by length (a
         // warp then walks rows of similar length); kept rows are found by id
@@ -346,11 +348,12 @@ __device__ __forceinline__ void rim_sector(const Plan &p, const QueryBufs &b, in
 // of up to kRegRow entries: every lane loads its own row into registers (all
 // loads of the warp in flight together), sorts it with the network that fits
 // the longest of them and leaves it in the warp's shared-memory tile, which
-// the warp stores row by row (coalesced).  Longer kept rows are sorted one at
-// a time across the warp's registers (two ids a lane up to 64 entries, four
-// up to kKeepRow).
+// the warp stores row by row (coalesced).  Longer kept rows are handled one
+// at a time by the whole warp: sorted across its registers up to
+// kCopySortRow entries (two ids a lane up to 64, four beyond), copied as kept
+// above that (the row sort orders them).
 constexpr int kCopyWarps = 8;
-static_assert(kKeepRow <= 128, "kept rows are sorted in four registers a lane");
+static_assert(kCopySortRow <= 128, "kept rows are sorted in at most four registers a lane");
 
 template <int N>
 __device__ __forceinline__ void sort_tile_row(int32_t (*T)[kRegRow + 1], const int32_t *__restrict__ src, int lane,
@@ -410,6 +413,10 @@ __global__ void __launch_bounds__(32 * kCopyWarps) k_rim_copy(Plan p, QueryBufs 
             const int32_t si = __shfl_sync(0xffffffffu, stored, i), di = __shfl_sync(0xffffffffu, deg, i);
             const int32_t oi = __shfl_sync(0xffffffffu, off, i);
             const int64_t bi = __shfl_sync(0xffffffffu, base, i);
+            if (di > kCopySortRow) {  // copied as kept; the row sort orders it
+                for (int32_t t = lane; t < di; t += 32) col_idx[bi + t] = b.small[si + t] - oi;
+                continue;
+            }
             if (di > 64) {  // four ids a lane
                 int32_t v[4];
 #pragma unroll

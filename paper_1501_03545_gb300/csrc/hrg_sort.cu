@@ -1,10 +1,10 @@
 // hrg_sort.cu -- ascending vertex ids inside every CSR row.
 //
 // The query traversal emits a row's neighbours in (band, angle) order.  The
-// canonical CSR lists each row ascending.  Rows kept by the rim count pass are
-// sorted by the copy that stores them, rows of up to kRegRow entries by the
-// traversal itself; the other rows (hub rows, longer rim rows traversed again)
-// are sorted here:
+// canonical CSR lists each row ascending.  Rows of up to kCopySortRow entries
+// kept by the rim count pass are sorted by the copy that stores them, rows of
+// up to kRegRow entries by the traversal itself; the other rows (hub rows,
+// longer rim rows, kept or traversed again) are sorted here:
 //   * kRegRow < d <= kWarpRow:  one warp per row; up to 64 ids by a bitonic
 //     network in the warp's registers, more by a bucket sort in the warp's
 //     shared-memory slice (the ids of a row are spread evenly over [0, n), so
