@@ -96,13 +96,14 @@ int fail(hrg_server *s, int code, const char *fmt, ...)
 
 // Device bytes of a request: outputs (r, phi, row offsets, neighbour ids at
 // 1.1 kbar per vertex) and the transient workspace of its generation (about
-// 200 bytes per vertex, the hub-entry pool included, plus the big-row sort
-// buffer).
+// 250 bytes per vertex: ~80 of band structure and per-vertex lists, 128 of
+// kept-row buffer, 32 of hub-entry pool; plus the big-row sort buffer at up
+// to 4 bytes per entry and the pool's fixed 64 MB).
 void estimate(const hrg_params &p, size_t &out, size_t &work)
 {
     const double n = (double)p.n, e = 1.1 * p.avg_degree * n + 1024.0;
     out = (size_t)(16.0 * n + 8.0 * (n + 1) + 4.0 * e) + 4096;
-    work = (size_t)(200.0 * n + 4.0 * e) + ((size_t)1 << 26);
+    work = (size_t)(250.0 * n + 4.0 * e) + ((size_t)1 << 26);
 }
 
 void run_batch(hrg_server *s, hrg_ctx *ctx, cudaStream_t st, std::vector<Req *> &batch)
