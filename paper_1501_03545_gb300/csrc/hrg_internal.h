@@ -177,7 +177,8 @@ cudaError_t launch_copy_hub(const QueryBufs &b, int32_t p_hub, int32_t n_runs, c
                             int32_t *col_idx, cudaStream_t s);
 cudaError_t launch_write_hub(const Plan &p, const QueryBufs &b, bool fp64_only, int32_t p_hub,
                              const int64_t *row_off, int32_t *col_idx, cudaStream_t s);
-// Rim rows: kept rows are sorted and copied, the others traversed again.
+// Rim rows: kept rows are copied (those of up to kCopySortRow entries sorted
+// on the way), the others traversed again.
 cudaError_t launch_write_rim(const Plan &p, const QueryBufs &b, bool fp64_only, const int64_t *row_off,
                              int32_t *col_idx, cudaStream_t s);
 int query_launches(const Plan &p, int32_t p_hub, bool write);
