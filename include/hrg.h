@@ -107,9 +107,10 @@ double hrg_expected_degree(int64_t n, double alpha, double R);
  * hrg_create / hrg_destroy -- a context bound to one CUDA device.  The context
  * owns a grow-only device workspace reused across calls; destroy frees it.
  * A generation's workspace (beside the caller's outputs) comes to about 250
- * bytes per vertex of the graph or batch (about 200 above n = 6.7e7, where
- * the buffer of kept rows stops growing at 2^31 ids), plus 64 MB, plus 4
- * bytes per entry of the rows longer than 12288 entries (their sort buffer).
+ * bytes per vertex of the graph or batch, plus 64 MB, plus 4 bytes per entry
+ * of the rows longer than 12288 entries (their sort buffer); less per vertex
+ * above n = 6.7e7, where the buffer of kept rows stops growing at 2^31 ids
+ * (~200 bytes at n = 1e8).
  * Errors: HRG_EINVAL (null out), HRG_ECUDA (device cannot be selected).
  */
 int hrg_create(hrg_ctx **out, int device);
