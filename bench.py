@@ -57,16 +57,21 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def source_hash():
-    """Hash of the dominant kernel's sources with comments and whitespace
-    taken out, so that only a change of the code voids the traffic record."""
+def code_digest(texts):
+    """Hash of C/CUDA sources with comments and whitespace taken out."""
     h = hashlib.sha256()
-    for f in ("hrg_query.cu", "hrg_common.cuh", "hrg_internal.h"):
-        src = open(os.path.join(ROOT, "paper_1501_03545_gb300", "csrc", f)).read()
+    for src in texts:
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
         h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
+
+
+def source_hash():
+    """Digest of the dominant kernel's sources: only a change of the code,
+    not of its comments, voids the traffic record."""
+    return code_digest(open(os.path.join(ROOT, "paper_1501_03545_gb300", "csrc", f)).read()
+                       for f in ("hrg_query.cu", "hrg_common.cuh", "hrg_internal.h"))
 
 
 class ClockSampler:
