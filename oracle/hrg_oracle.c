@@ -471,17 +471,72 @@ void orc_bands_rows(void *h, const double *r, const double *phi, int64_t nq, con
 
 /* Tie band over the candidates of windows widened to the radius Rw with
  * cosh Rw = (1 + 2 tol) cosh R, which contain every pair within the
- * tolerance.  Pairs (i<j), serial so the list is in (i, j) order. */
+ * tolerance.  Queries run in parallel; each thread keeps the pairs it finds
+ * in a list of its own, and the lists are joined and sorted, so the result
+ * is the (i, j)-ordered list whatever the thread count.  Writes up to cap
+ * pairs (i<j) and returns how many exist. */
+int orc_num_threads(void);
+typedef struct { int64_t *p; int64_t len, cap; } orc_pairlist;
+
+static void pairlist_add(orc_pairlist *L, const int64_t *pairs, int64_t k)
+{
+    if (L->len + k > L->cap) {
+        int64_t c = L->cap ? 2 * L->cap : 64;
+        while (c < L->len + k) c *= 2;
+        L->p = (int64_t *)realloc(L->p, sizeof(int64_t) * 2 * (size_t)c);
+        L->cap = c;
+    }
+    memcpy(L->p + 2 * L->len, pairs, sizeof(int64_t) * 2 * (size_t)k);
+    L->len += k;
+}
+
+static int cmp_pair(const void *a, const void *b)
+{
+    const int64_t *x = (const int64_t *)a, *y = (const int64_t *)b;
+    if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
+    return (x[1] > y[1]) - (x[1] < y[1]);
+}
+
 int64_t orc_bands_ties(void *h, const double *r, const double *phi, double tol, int64_t cap, int64_t *pairs)
 {
     orc_bands *B = (orc_bands *)h;
     double Rw = acosh(B->cR * (1.0 + 2.0 * tol));
-    int64_t cnt = 0;
-    for (int64_t i = 0; i < B->n; ++i) {
-        int64_t room = cap > cnt ? cap - cnt : 0;
-        int64_t got = band_query(B, r[i], phi[i], (int32_t)i, NULL, Rw, tol, room, pairs + 2 * (cnt < cap ? cnt : cap));
-        cnt += got;
+    int nt = orc_num_threads();
+    orc_pairlist *lists = (orc_pairlist *)calloc((size_t)nt, sizeof(orc_pairlist));
+    #pragma omp parallel
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        int64_t room = 64;
+        int64_t *buf = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)room);
+        #pragma omp for schedule(dynamic, 256)
+        for (int64_t i = 0; i < B->n; ++i) {
+            int64_t got = band_query(B, r[i], phi[i], (int32_t)i, NULL, Rw, tol, room, buf);
+            if (got > room) { /* more than fit: ask again with room for all */
+                room = got;
+                buf = (int64_t *)realloc(buf, sizeof(int64_t) * 2 * (size_t)room);
+                got = band_query(B, r[i], phi[i], (int32_t)i, NULL, Rw, tol, room, buf);
+            }
+            if (got > 0) pairlist_add(&lists[t], buf, got);
+        }
+        free(buf);
     }
+    int64_t cnt = 0;
+    for (int t = 0; t < nt; ++t) cnt += lists[t].len;
+    int64_t *all = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(cnt > 0 ? cnt : 1));
+    int64_t k = 0;
+    for (int t = 0; t < nt; ++t) {
+        if (lists[t].len) memcpy(all + 2 * k, lists[t].p, sizeof(int64_t) * 2 * (size_t)lists[t].len);
+        k += lists[t].len;
+        free(lists[t].p);
+    }
+    free(lists);
+    qsort(all, (size_t)cnt, sizeof(int64_t) * 2, cmp_pair);
+    int64_t w = cnt < cap ? cnt : cap;
+    if (w > 0) memcpy(pairs, all, sizeof(int64_t) * 2 * (size_t)w);
+    free(all);
     return cnt;
 }
 

@@ -385,6 +385,30 @@ def test_band_algorithm_equals_brute_force_injected(kind):
     assert ka == kb and np.array_equal(np.sort(pa, axis=0), np.sort(pb, axis=0))
 
 
+@pytest.mark.parametrize("threads", [1, 0])
+def test_band_tie_listing_equals_brute_force(threads):
+    """The band algorithm's tie listing (queries in parallel, per-thread lists
+    joined and sorted) lists exactly the all-pairs scan's pairs, in the same
+    (i, j) order, at any thread count.  A wide tolerance (1e-3, 1e-2) makes
+    hundreds of pairs near the threshold, several per row."""
+    R = 14.0
+    r, phi = W.random_points(2500, R, 31)
+    full = O.num_threads()
+    try:
+        if threads:
+            O.set_threads(threads)
+        for tol in (1e-3, 1e-2):
+            ka, pa = O.brute_ties(r, phi, R, tol=tol)
+            kb, pb = O.Bands(r, phi, R).ties(tol=tol)
+            assert ka > 100 and ka == kb
+            assert np.array_equal(pa, pb)
+            # a short output buffer keeps the first pairs and still counts all
+            kc, pc = O.Bands(r, phi, R).ties(tol=tol, cap=7)
+            assert kc == ka and np.array_equal(pc, pa[:7])
+    finally:
+        O.set_threads(full)
+
+
 def test_mean_degree_matches_exact_expectation():
     """Measured 2m/n over 8 seeds against the quadrature expectation at the
     solved R, 4 sigma from the seeds' own spread."""
