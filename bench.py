@@ -548,8 +548,10 @@ def main():
                            "l2": "no flush: every step writes and reads >8 GB, far above the 126 MB L2"},
                 "fp64_plain": fp64, "batched": batched, "serving": serving, "properties": props, "stage_ms": stage, "e2e": e2e, "roofline": roof, "clocks": clocks,
                 "cpu_baseline": cpu, "paper_quadtree": quadtree, "gpu_launches": last.get("launches", 0) * args.steps,
-                "job": {k: last[k] for k in ("R", "candidates", "rechecks", "bands", "hub_bands", "buckets",
-                                             "hub_queries", "mid_rows", "big_rows", "mu")}}
+                "ties": last["ties"],
+                "job": {k: last[k] for k in ("R", "candidates", "rechecks", "ties", "bands", "hub_bands", "buckets",
+                                             "hub_queries", "mid_rows", "big_rows", "mu", "rows_no_room",
+                                             "hub_rows_retraversed", "heavy_retries")}}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:

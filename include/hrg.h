@@ -84,6 +84,19 @@ typedef struct hrg_stats {
      * rim-band vertices, [7] row sort */
     float stage_ms[8];
     int32_t launches;            /* kernels this library launched for the job       */
+    /* the tie band: candidate pairs whose FP64 value cosh d lies within
+     * 1e-12 cosh R of cosh R (relative), each pair counted once.  Two
+     * correct FP64 evaluations of such a pair may decide it differently, so
+     * it is the only place an exact comparison may differ; expected ~0. */
+    uint64_t ties;
+    /* fallbacks of the count pass (they change the speed, never the graph):
+     * rim rows it found no room to keep (the write pass traverses them
+     * again), hub rows traversed again because the pool of hub ids or its run
+     * table overflowed (0 when the pool held them all), and count passes run
+     * again because the list of long hub ranges overflowed */
+    int64_t rows_no_room;
+    int32_t hub_rows_retraversed;
+    int32_t heavy_retries;
 } hrg_stats;
 
 typedef struct hrg_ctx hrg_ctx;
@@ -182,6 +195,32 @@ int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_params *item
  */
 int hrg_generate_finish(hrg_job *job, int32_t *col_idx_out);
 
+/*
+ * hrg_set_limits -- capacities of the buffers the count pass fills for the
+ * write pass, for a context's later jobs (0 or a null lim: automatic).  A
+ * smaller buffer means less workspace and more work, never another graph:
+ *   row_buffer_ids  ids of the buffer of kept rim rows (automatic: 32 per
+ *                   vertex, below 2^31); rows that find no room are
+ *                   traversed again by the write pass (rows_no_room)
+ *   hub_pool_ids    ids of the pool of hub-row entries (automatic: 8 per
+ *                   vertex + 2^24), below 2^40; hub_runs: entries of its run
+ *                   table (automatic from the pool size), below 2^24.  When
+ *                   either overflows, the write pass traverses every hub row
+ *                   again (hub_rows_retraversed)
+ *   heavy_segments  first capacity of the list of long hub ranges (automatic:
+ *                   max(2^16, n/64)); when it overflows the count pass runs
+ *                   once more with room for all (heavy_retries)
+ * Errors: HRG_EINVAL (negative or oversized value), HRG_ESTATE (a job is open).
+ */
+typedef struct hrg_limits {
+    int64_t row_buffer_ids;
+    int64_t hub_pool_ids;
+    int32_t hub_runs;
+    int32_t heavy_segments;
+} hrg_limits;
+
+int hrg_set_limits(hrg_ctx *ctx, const hrg_limits *lim);
+
 /* Statistics of a job (after begin; candidate counts from the count pass). */
 int hrg_job_stats(const hrg_job *job, hrg_stats *out);
 
@@ -228,6 +267,9 @@ int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_host, double 
  * every device that loads the library until the process exits.  The first
  * call on a device looks up that array's device address (with the device
  * current), so make the first call on each device before any stream capture.
+ * The library caches that address per device for the life of the process; a
+ * cudaDeviceReset invalidates it, so do not call this entry point on a device
+ * after resetting it.
  * All calls share the array: calls whose executions overlap on the GPU (on
  * different streams, or from different threads) race and corrupt each other's
  * results; serialize them.

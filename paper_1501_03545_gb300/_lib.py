@@ -23,7 +23,7 @@ EXPORTS = (
     "hrg_generate", "hrg_generate_host", "hrg_last_error", "hrg_version", "hrg_row_offsets_noalloc",
     "hrg_generate_batch_begin", "hrg_server_create", "hrg_server_submit", "hrg_server_wait", "hrg_server_release",
     "hrg_server_stats", "hrg_server_last_error", "hrg_server_destroy", "hrg_graph_props", "hrg_degree_histogram",
-    "hrg_add_random_edges", "hrg_bfs", "hrg_diameter_bounds",
+    "hrg_add_random_edges", "hrg_bfs", "hrg_diameter_bounds", "hrg_set_limits",
 )
 HRG_PROPS_TRIANGLES = 0x1
 
@@ -45,7 +45,9 @@ class hrg_stats(ctypes.Structure):
                 ("rechecks", ctypes.c_uint64), ("bands", ctypes.c_int32), ("hub_bands", ctypes.c_int32),
                 ("buckets", ctypes.c_int64), ("hub_queries", ctypes.c_int32), ("mid_rows", ctypes.c_int32),
                 ("big_rows", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mu", ctypes.c_float),
-                ("stage_ms", ctypes.c_float * 8), ("launches", ctypes.c_int32)]
+                ("stage_ms", ctypes.c_float * 8), ("launches", ctypes.c_int32), ("ties", ctypes.c_uint64),
+                ("rows_no_room", ctypes.c_int64), ("hub_rows_retraversed", ctypes.c_int32),
+                ("heavy_retries", ctypes.c_int32)]
 
     STAGES = ("sample", "bands", "count_hub", "count_rim", "offsets", "write_hub", "write_rim", "rowsort")
 
@@ -53,6 +55,11 @@ class hrg_stats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "stage_ms")}
         d["stage_ms"] = {s: float(self.stage_ms[i]) for i, s in enumerate(self.STAGES)}
         return d
+
+
+class hrg_limits(ctypes.Structure):
+    _fields_ = [("row_buffer_ids", ctypes.c_int64), ("hub_pool_ids", ctypes.c_int64), ("hub_runs", ctypes.c_int32),
+                ("heavy_segments", ctypes.c_int32)]
 
 
 class hrg_props(ctypes.Structure):
@@ -122,6 +129,7 @@ def load(build_if_missing: bool = True):
         L.hrg_bfs.argtypes = [_P, _I64, _P, _P, _I64, _P, _P, ctypes.POINTER(ctypes.c_int32), _PI64, _PI64, _PI64]
         L.hrg_diameter_bounds.argtypes = [_P, _I64, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32), _PI64, _PI64]
+        L.hrg_set_limits.argtypes = [_P, ctypes.POINTER(hrg_limits)]
         L.hrg_add_random_edges.argtypes = [_P, _I64, _P, _P, _I64, ctypes.c_uint64, _P, _P, _P, _I64, _PI64, _PI64]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
@@ -186,6 +194,12 @@ class Context:
     def check(self, rc):
         if rc != HRG_OK:
             raise HrgError(rc, self.last_error())
+
+    def set_limits(self, row_buffer_ids=0, hub_pool_ids=0, hub_runs=0, heavy_segments=0):
+        """hrg_set_limits: capacities of the count pass's buffers for later
+        jobs (0: automatic)."""
+        lim = hrg_limits(int(row_buffer_ids), int(hub_pool_ids), int(hub_runs), int(heavy_segments))
+        self.check(load().hrg_set_limits(self.h, ctypes.byref(lim)))
 
 
 def params(n, alpha, avg_degree, seed, R_override=0.0, fp64_only=False, bands=0, hub_candidates=0) -> hrg_params:
@@ -406,12 +420,23 @@ def generate_host(ctx: Context, n, alpha, avg_degree, seed, r_host, phi_host, of
 
 def hrg_row_offsets_noalloc(deg, row_off, stream=None) -> int:
     """Row offsets from int32 degrees (device tensors) using the library's
-    static scratch; returns the status code."""
+    static scratch; returns the status code.  deg: contiguous int32[n];
+    row_off: contiguous int64 with at least n + 1 elements, on deg's device
+    (ValueError otherwise).  The call runs with that device current."""
     import torch
 
-    st = stream if stream is not None else torch.cuda.current_stream(deg.device)
-    return int(load().hrg_row_offsets_noalloc(_P(deg.data_ptr()), int(deg.numel()), _P(row_off.data_ptr()),
-                                              _P(st.cuda_stream)))
+    if not (deg.is_cuda and row_off.is_cuda and deg.device == row_off.device):
+        raise ValueError("deg and row_off must be CUDA tensors on one device")
+    if deg.dtype != torch.int32 or row_off.dtype != torch.int64:
+        raise ValueError("deg must be int32 and row_off int64")
+    if not (deg.is_contiguous() and row_off.is_contiguous()):
+        raise ValueError("deg and row_off must be contiguous")
+    if row_off.numel() < deg.numel() + 1:
+        raise ValueError("row_off needs n + 1 = %d elements, has %d" % (deg.numel() + 1, row_off.numel()))
+    with torch.cuda.device(deg.device):
+        st = stream if stream is not None else torch.cuda.current_stream(deg.device)
+        return int(load().hrg_row_offsets_noalloc(_P(deg.data_ptr()), int(deg.numel()), _P(row_off.data_ptr()),
+                                                  _P(st.cuda_stream)))
 
 
 class Server:

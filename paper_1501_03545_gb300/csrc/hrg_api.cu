@@ -88,6 +88,7 @@ struct hrg_job {
     bool sampled = false;  // points drawn by the generator (else injected)
     bool hub_pooled = false;  // the count pass kept every hub entry: the write pass copies them
     int32_t hub_runs = 0;
+    int32_t heavy_retries = 0;  // count passes repeated for lack of room in the list of long hub ranges
     bool open = false;
     bool finished = false;
     int32_t p_hub = 0;
@@ -120,6 +121,7 @@ struct hrg_ctx {
     cudaEvent_t ev[10] = {};  // stage boundaries of the current job
     cudaStream_t work = nullptr, copy = nullptr;  // hrg_generate_host: generation and read-back streams
     hrg_job job;
+    hrg_limits lim{};  // capacities of the count pass's buffers (0: automatic)
     std::vector<Plan> batch_plans;  // host plans of the current batch
     std::vector<int64_t> batch_noff, batch_soff;
 };
@@ -225,6 +227,19 @@ extern "C" int hrg_destroy(hrg_ctx *ctx)
     return HRG_OK;
 }
 
+extern "C" int hrg_set_limits(hrg_ctx *ctx, const hrg_limits *lim)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (ctx->job.open) return set_err(ctx, HRG_ESTATE, "a job of this context is still open");
+    hrg_limits l{};
+    if (lim) l = *lim;
+    if (l.row_buffer_ids < 0 || l.hub_pool_ids < 0 || l.hub_pool_ids >= (1LL << 40) || l.hub_runs < 0 ||
+        l.hub_runs >= (1 << 24) || l.heavy_segments < 0)
+        return set_err(ctx, HRG_EINVAL, "limits out of range");
+    ctx->lim = l;
+    return HRG_OK;
+}
+
 extern "C" const char *hrg_last_error(const hrg_ctx *ctx)
 {
     if (!ctx) return "null context";
@@ -264,6 +279,9 @@ static void plan_bands(Plan &p, int64_t n, double R, double alpha, int bands)
     }
     p.rhs64 = 1.0 + std::exp(-2.0 * R);
     p.rhs32 = f32(p.rhs64);
+    const double tie_lo = p.rhs64 - 1e-12 * p.rhs64, tie_hi = p.rhs64 + 1e-12 * p.rhs64;
+    memcpy(&p.tie_lo, &tie_lo, 8);
+    memcpy(&p.tie_hi, &tie_hi, 8);
     // Undecided band of the FP32 filter: the FP32 value carries a relative
     // error below ~2^-19 from its inputs and operations, plus the difference
     // between the fixed-point angle and the FP64 angles (<= ~2e-15 rad
@@ -346,7 +364,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     b.big_total = (int64_t *)bigtot;
     // heavy hub segments (long hub ranges cut into CTA chunks) and hub row cursors
     void *heavy = nullptr, *cursor = nullptr, *wcnt = nullptr, *scnt = nullptr;
-    int64_t heavy_cap = std::max<int64_t>(1 << 16, n / 64);
+    int64_t heavy_cap = ctx->lim.heavy_segments > 0 ? ctx->lim.heavy_segments : std::max<int64_t>(1 << 16, n / 64);
     if (J.p_hub > 0) {
         if ((rc = ensure(ctx, hrg_ctx::W_CURSOR, sizeof(int32_t) * J.p_hub, &cursor))) return rc;
         if ((rc = ensure(ctx, hrg_ctx::W_WARPCNT, sizeof(int32_t) * J.p_hub, &wcnt))) return rc;
@@ -357,7 +375,8 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     // entries per vertex, below 2^31 in all; rows that find none are
     // traversed again)
     void *small = nullptr, *small_off = nullptr, *small_cur = nullptr;
-    const int64_t small_cap = small_capacity(n);
+    const int64_t small_cap =
+        ctx->lim.row_buffer_ids > 0 ? std::min(ctx->lim.row_buffer_ids, small_capacity(n)) : small_capacity(n);
     if ((rc = ensure(ctx, hrg_ctx::W_SMALL, small_bytes(n), &small))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SMALLOFF, sizeof(int32_t) * n, &small_off))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SMALLCUR, sizeof(unsigned long long), &small_cur))) return rc;
@@ -369,7 +388,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
     // the hub rows' ids, kept by the count pass in runs (room for 8 per vertex:
     // on overflow the write pass traverses the hub rows again instead)
     void *pool = nullptr, *runs = nullptr, *pool_cur = nullptr;
-    const int64_t pool_cap = 8 * n + (1 << 24);
+    const int64_t pool_cap = ctx->lim.hub_pool_ids > 0 ? ctx->lim.hub_pool_ids : 8 * n + (1 << 24);
     if (J.p_hub > 0) {
         if ((rc = ensure(ctx, hrg_ctx::W_HPOOL, sizeof(int32_t) * pool_cap, &pool))) return rc;
         if ((rc = ensure(ctx, hrg_ctx::W_HPCUR, sizeof(unsigned long long), &pool_cur))) return rc;
@@ -382,7 +401,9 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
         b.seg_cnt = (int32_t *)scnt;
         b.heavy_cap = (int32_t)heavy_cap;
         // a warp's runs hold at least 1024 - 64 ids, except its last one and one per heavy chunk
-        const int64_t run_cap = std::min<int64_t>(pool_cap / 512 + J.p_hub + heavy_cap + 1024, (1 << 24) - 1);
+        const int64_t run_cap = ctx->lim.hub_runs > 0
+                                    ? ctx->lim.hub_runs
+                                    : std::min<int64_t>(pool_cap / 512 + J.p_hub + heavy_cap + 1024, (1 << 24) - 1);
         if (J.p_hub > 0) {
             if ((rc = ensure(ctx, hrg_ctx::W_HRUNS, sizeof(int4) * run_cap, &runs))) return rc;
             CK(cudaMemsetAsync(pool_cur, 0, sizeof(unsigned long long), st));
@@ -429,6 +450,7 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
         // grow the list and count again
         if (attempt > 0 || heavy_found > (1 << 30)) return set_err(ctx, HRG_EINTERNAL, "heavy segment list overflow");
         heavy_cap = (int64_t)heavy_found + heavy_found / 8 + 1024;
+        J.heavy_retries = attempt + 1;
     }
     memcpy(&J.n_entries, hp + 0, 8);
     memcpy(J.lists, hp + 8, 12);
@@ -834,6 +856,10 @@ extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
     out->big_rows = job->lists[2];
     out->mu = job->plan.mu;
     for (int k = 0; k < 8; ++k) out->stage_ms[k] = job->stage_ms[k];
+    out->ties = job->stats[3];
+    out->rows_no_room = (int64_t)job->stats[4];
+    out->hub_rows_retraversed = (job->p_hub > 0 && !job->hub_pooled) ? job->p_hub : 0;
+    out->heavy_retries = job->heavy_retries;
     // kernels launched: points with their buckets (1; an injected point set:
     // band counts + bucket histogram, 2), bucket scan, structure-of-arrays
     // scatter (records + split, 2; the FP64 path 1), count (hub 3, rim 1),

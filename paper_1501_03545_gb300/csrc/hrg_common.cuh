@@ -38,6 +38,10 @@ struct Plan {
     float rhs32;         // 1 + e^{-2R} rounded to float
     float mu;            // half-width of the FP32 filter's undecided band (relative)
     double rhs64;        // 1 + e^{-2R}
+    // the tie band of the FP64 path's scaled value: the bit patterns of
+    // rhs64 (1 - 1e-12) and rhs64 (1 + 1e-12) (positive doubles order like
+    // their bits, so the band test is two integer compares)
+    int64_t tie_lo, tie_hi;
     // A batch of graphs lays its graphs out one after another: graph g owns
     // positions and global ids [id_off, id_off + n) and buckets from base[0].
     // The CSR stores local ids (global id - id_off).  0 for a single graph.
@@ -263,7 +267,7 @@ __device__ __forceinline__ double sin_small64(double x)
 // reference form of the predicate): cosh(r1-r2) + 2 sinh r1 sinh r2 s^2 < cosh R
 // with s = sin((phi1 - phi2)/2) computed from the same doubles the caller
 // sees.  Relative error a few ulp, far inside the 1e-12 tie band.
-__device__ __forceinline__ bool edge64(double r1, double phi1, double r2, double phi2, double coshR)
+__device__ __forceinline__ double cosh_dist64(double r1, double phi1, double r2, double phi2)
 {
     // fixed operand order: both endpoints of a pair get the same value
     if (r1 > r2 || (r1 == r2 && phi1 > phi2)) {
@@ -271,9 +275,18 @@ __device__ __forceinline__ bool edge64(double r1, double phi1, double r2, double
         r1 = r2; phi1 = phi2; r2 = tr; phi2 = tp;
     }
     const double s = sin_small64(0.5 * (phi1 - phi2));
-    const double v = cosh(r1 - r2) + 2.0 * sinh(r1) * sinh(r2) * (s * s);
-    return v < coshR;
+    return cosh(r1 - r2) + 2.0 * sinh(r1) * sinh(r2) * (s * s);
 }
+
+__device__ __forceinline__ bool edge64(double r1, double phi1, double r2, double phi2, double coshR)
+{
+    return cosh_dist64(r1, phi1, r2, phi2) < coshR;
+}
+
+// The tie band: pairs whose FP64 value lies within 1e-12 of the threshold
+// (relative).  Their decision may differ between two correct FP64
+// evaluations (a few ulp of rounding), so they are counted, not trusted.
+constexpr double kTieBand = 1e-12;
 
 // FP64 per-point data of the plain double-precision path
 struct __align__(16) PMS64 { double P, M, S, phi; };
@@ -288,14 +301,19 @@ __device__ __forceinline__ PMS64 scaled_exps64(const Plan &p, double r, double p
     return o;
 }
 
-__device__ __forceinline__ bool edge_pms64(const Plan &p, const PMS64 &q, const PMS64 &c)
+// P1 M2 + P2 M1 + S1 S2 sin^2(dphi/2), to be compared with 1 + e^{-2R}
+__device__ __forceinline__ double lhs_pms64(const PMS64 &q, const PMS64 &c)
 {
     // fixed operand order: both endpoints of a pair get the same value
     const bool sw = q.P > c.P || (q.P == c.P && q.phi > c.phi);
     const PMS64 &a = sw ? c : q, &b = sw ? q : c;
     const double s = sin_small64(0.5 * (a.phi - b.phi));
-    const double v = fma(a.S * b.S, s * s, fma(a.P, b.M, b.P * a.M));
-    return v < p.rhs64;
+    return fma(a.S * b.S, s * s, fma(a.P, b.M, b.P * a.M));
+}
+
+__device__ __forceinline__ bool edge_pms64(const Plan &p, const PMS64 &q, const PMS64 &c)
+{
+    return lhs_pms64(q, c) < p.rhs64;
 }
 
 // ---------------------------------------------------------------------------

@@ -28,7 +28,7 @@ namespace hrg {
 
 namespace {
 
-enum { ST_CAND = 0, ST_RECHECK = 1, ST_EDGES = 2, ST_ERR = 7 };
+enum { ST_CAND = 0, ST_RECHECK = 1, ST_EDGES = 2, ST_TIES = 3, ST_NOROOM = 4, ST_ERR = 7 };
 
 
 
@@ -73,6 +73,10 @@ __device__ __forceinline__ bool within(uint64_t Aq, uint64_t Ac, uint64_t W)
 }
 
 // Decide candidate c (position cpos, data already loaded) for query q.
+// n_re counts the FP64 rechecks in its low 24 bits and, above them, the
+// pairs of the tie band (each pair once: from its smaller id); one counter
+// keeps the register budget of the hot loop.
+constexpr unsigned kTieUnit = 1u << 24;
 template <bool F64>
 __device__ __forceinline__ bool decide_loaded(const Plan &p, const QueryBufs &b, const PMS &q, const PMS64 &q64,
                                               uint64_t Aq, uint64_t Ac, const PMS &cc, int32_t cpos, uint64_t W,
@@ -82,29 +86,35 @@ __device__ __forceinline__ bool decide_loaded(const Plan &p, const QueryBufs &b,
     ++n_cand;
     if (F64) {
         const PMS64 c64 = b.pms64[cpos];
-        return edge_pms64(p, q64, c64);
+        const double v = lhs_pms64(q64, c64);
+        const long long vb = __double_as_longlong(v);
+        if (vb > p.tie_lo && vb < p.tie_hi && q.id < cc.id) n_re += kTieUnit;
+        return v < p.rhs64;
     } else {
         const float v = lhs32(q, cc, (int64_t)(Ac - Aq));
         if (v < p.rhs32 * (1.0f - p.mu)) return true;
         if (v > p.rhs32 * (1.0f + p.mu)) return false;
-        ++n_re;
-        return edge64(__ldg(b.r + q.id), __ldg(b.phi + q.id), __ldg(b.r + cc.id), __ldg(b.phi + cc.id), p.coshR);
+        const double d = cosh_dist64(__ldg(b.r + q.id), __ldg(b.phi + q.id), __ldg(b.r + cc.id), __ldg(b.phi + cc.id));
+        n_re += 1u + ((fabs(d - p.coshR) < kTieBand * p.coshR && q.id < cc.id) ? kTieUnit : 0u);
+        return d < p.coshR;
     }
 }
 
 __device__ __forceinline__ void add_stats(unsigned long long *stats, unsigned n_cand, unsigned n_re, unsigned n_edge)
 {
-    unsigned long long a = n_cand, r = n_re, e = n_edge;
+    unsigned long long a = n_cand, r = n_re & (kTieUnit - 1u), e = n_edge, t = n_re / kTieUnit;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, o);
         r += __shfl_down_sync(0xffffffffu, r, o);
         e += __shfl_down_sync(0xffffffffu, e, o);
+        t += __shfl_down_sync(0xffffffffu, t, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (a) atomicAdd(&stats[ST_CAND], a);
         if (r) atomicAdd(&stats[ST_RECHECK], r);
         if (e) atomicAdd(&stats[ST_EDGES], e);
+        if (t) atomicAdd(&stats[ST_TIES], t);
     }
 }
 
@@ -250,6 +260,8 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
             if (keep && pos + cnt <= b.small_cap) {
                 for (int32_t k = 0; k < cnt; ++k) b.small[pos + k] = buf[k];
                 off = (int32_t)pos;
+            } else if (keep) {
+                atomicAdd(&b.stats[ST_NOROOM], 1ull);  // kept nowhere: the write pass traverses it again
             }
             b.small_off[qp] = off;
             b.deg[q.id] = cnt;

@@ -24,6 +24,13 @@ def H():
     return _lib
 
 
+def _cumsum_offsets(deg):
+    """Independent reference: torch's own prefix sum, with the leading 0."""
+    ref = torch.zeros(deg.numel() + 1, dtype=torch.int64, device=deg.device)
+    ref[1:] = torch.cumsum(deg.to(torch.int64), 0)
+    return ref
+
+
 def test_noalloc_row_offsets_match_generator(H):
     ctx = H.Context(0)
     try:
@@ -38,8 +45,38 @@ def test_noalloc_row_offsets_match_generator(H):
             assert rc == H.HRG_OK
             torch.cuda.synchronize()
             assert torch.equal(out, ref), (n, int((out != ref).sum()))
+            assert torch.equal(out, _cumsum_offsets(deg))
     finally:
         ctx.close()
+
+
+def test_noalloc_two_level_scan_matches_cumsum(H):
+    """Sizes above 4096 tiles of 4096 degrees run the scan's second level
+    from the static scratch too: two calls in a row with different contents
+    (and the largest size the scratch admits) against torch.cumsum."""
+    g = torch.Generator(device="cuda").manual_seed(11)
+    for n in ((1 << 24) + 12345, (1 << 28)):
+        for hi in (40, 3):
+            deg = torch.randint(0, hi, (n,), device="cuda", dtype=torch.int32, generator=g)
+            out = torch.full((n + 1,), -1, dtype=torch.int64, device="cuda")
+            assert H.hrg_row_offsets_noalloc(deg, out) == H.HRG_OK
+            torch.cuda.synchronize()
+            assert torch.equal(out, _cumsum_offsets(deg)), (n, hi)
+            del deg, out
+
+
+def test_noalloc_binding_checks_arguments(H):
+    deg = torch.zeros(10, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):
+        H.hrg_row_offsets_noalloc(deg, torch.zeros(10, dtype=torch.int64, device="cuda"))  # too short
+    with pytest.raises(ValueError):
+        H.hrg_row_offsets_noalloc(deg.to(torch.int64), torch.zeros(11, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        H.hrg_row_offsets_noalloc(deg, torch.zeros(11, dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):
+        H.hrg_row_offsets_noalloc(deg[::2], torch.zeros(6, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        H.hrg_row_offsets_noalloc(deg.cpu(), torch.zeros(11, dtype=torch.int64))
 
 
 def test_noalloc_rejects_sizes_beyond_maximum(H):
