@@ -185,6 +185,45 @@ int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_params *item
                              int64_t *n_entries);
 
 /*
+ * hrg_update_begin -- vertex movement.  The paper's conclusion names a
+ * dynamic model, in which vertices move and the incremental quadtree follows
+ * them, as future work, and defines no movement law; so the moves are an
+ * input: vertex ids[i] moves to (r_new[i], phi_new[i]).  The result is the
+ * threshold graph (Sec. 2.1's edge rule) of the updated point set -- the
+ * graph hrg_generate_from_points_begin builds from it -- as a canonical CSR
+ * (rows ascending, symmetric, no self-loops).  Finish with
+ * hrg_generate_finish(job, col_idx_out), col_idx_out of *n_entries entries.
+ *   n, R        the graph's vertex count (1 <= n < 2^31) and disk radius
+ *   r, phi      device double[n]: the current points (caller owned), changed
+ *               in place to the updated ones once the moves are accepted
+ *   row_off, col_idx  device: the current canonical CSR of (r, phi) (read;
+ *               both must stay untouched until finish; row_off[0] may be
+ *               non-zero)
+ *   k           0 <= k <= n moved vertices; ids device int32[k], distinct,
+ *               in [0, n); r_new, phi_new device double[k], 0 <= r_new < R,
+ *               0 <= phi_new < 2pi
+ *   flags       HRG_FLAG_FP64_ONLY as for generation; bands as for
+ *               hrg_generate_from_points_begin
+ *   row_off_out device int64[n+1] (caller owned): the new row offsets, from 0
+ * Work: the band structure is rebuilt from the updated points (no sampling);
+ * only the k moved vertices are queried; every other row changes only by the
+ * moved vertices it loses (those in its old row) and gains (those whose new
+ * row holds it), so untouched rows are copied and the rest compacted or
+ * merged.  The call synchronizes the stream (read-backs of the check and of
+ * the totals).  hrg_job_stats reports the moved queries' candidates,
+ * rechecks and ties; its stage times are [0] band counts, [1] band
+ * structure, [2] moved vertices counted, [3] removals and degrees, [4] row
+ * offsets, [5] moved rows written, [6] other rows copied, [7] row sort.
+ * Errors: HRG_EINVAL (sizes, null pointers, an id out of range or repeated, a
+ * coordinate outside [0, R) x [0, 2pi) -- then r and phi are unchanged),
+ * HRG_ESTATE, HRG_ENOMEM, HRG_ECUDA.
+ */
+int hrg_update_begin(hrg_ctx *ctx, int64_t n, double R, double *r, double *phi, const int64_t *row_off,
+                     const int32_t *col_idx, int64_t k, const int32_t *ids, const double *r_new,
+                     const double *phi_new, uint32_t flags, int32_t bands, void *stream, int64_t *row_off_out,
+                     hrg_job **job, int64_t *n_entries);
+
+/*
  * hrg_generate_finish -- the edge insertion of Algorithm 1: writes the
  * neighbour ids of every vertex into col_idx_out (device int32[n_entries],
  * caller owned) at the offsets produced by begin, each row ascending.

@@ -23,7 +23,7 @@ EXPORTS = (
     "hrg_generate", "hrg_generate_host", "hrg_last_error", "hrg_version", "hrg_row_offsets_noalloc",
     "hrg_generate_batch_begin", "hrg_server_create", "hrg_server_submit", "hrg_server_wait", "hrg_server_release",
     "hrg_server_stats", "hrg_server_last_error", "hrg_server_destroy", "hrg_graph_props", "hrg_degree_histogram",
-    "hrg_add_random_edges", "hrg_bfs", "hrg_diameter_bounds", "hrg_set_limits",
+    "hrg_add_random_edges", "hrg_bfs", "hrg_diameter_bounds", "hrg_set_limits", "hrg_update_begin",
 )
 HRG_PROPS_TRIANGLES = 0x1
 
@@ -130,6 +130,8 @@ def load(build_if_missing: bool = True):
         L.hrg_diameter_bounds.argtypes = [_P, _I64, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32), _PI64, _PI64]
         L.hrg_set_limits.argtypes = [_P, ctypes.POINTER(hrg_limits)]
+        L.hrg_update_begin.argtypes = [_P, _I64, ctypes.c_double, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_uint32,
+                                       ctypes.c_int32, _P, _P, ctypes.POINTER(_P), _PI64]
         L.hrg_add_random_edges.argtypes = [_P, _I64, _P, _P, _I64, ctypes.c_uint64, _P, _P, _P, _I64, _PI64, _PI64]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
@@ -393,6 +395,44 @@ def generate_from_points(ctx: Context, r, phi, R, fp64_only=False, bands=0, stre
                                                HRG_FLAG_FP64_ONLY if fp64_only else 0, int(bands),
                                                _P(st.cuda_stream), _P(_dptr(off)), ctypes.byref(job),
                                                ctypes.byref(ne)))
+    try:
+        col = torch.empty(max(ne.value, 1), dtype=torch.int32, device=dev)
+        ctx.check(L.hrg_generate_finish(job, _P(_dptr(col))))
+        s = hrg_stats()
+        L.hrg_job_stats(job, ctypes.byref(s))
+    finally:
+        L.hrg_job_release(job)
+    return {"row_off": off, "col_idx": col[: ne.value], "stats": s.as_dict()}
+
+
+def update_points(ctx: Context, r, phi, row_off, col_idx, R, ids, r_new, phi_new, fp64_only=False, bands=0,
+                  stream=None):
+    """hrg_update_begin + hrg_generate_finish: k = len(ids) vertices move to
+    (r_new, phi_new).  r, phi (device float64[n]) are updated in place;
+    row_off, col_idx are the current CSR.  Returns the new row_off, col_idx
+    (torch tensors) and stats."""
+    import torch
+
+    L = load()
+    n = r.numel()
+    dev = r.device
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    ids = ids.to(device=dev, dtype=torch.int32).contiguous()
+    r_new = r_new.to(device=dev, dtype=torch.float64).contiguous()
+    phi_new = phi_new.to(device=dev, dtype=torch.float64).contiguous()
+    k = ids.numel()
+    if r_new.numel() != k or phi_new.numel() != k:
+        raise ValueError("ids, r_new and phi_new must have the same length")
+    if not (r.is_contiguous() and phi.is_contiguous() and r.dtype == torch.float64 and phi.dtype == torch.float64):
+        raise ValueError("r and phi must be contiguous float64 device tensors")
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    job = _P()
+    ne = ctypes.c_int64()
+    col_in = _P(_dptr(col_idx)) if col_idx.numel() > 0 else _P(None)
+    ctx.check(L.hrg_update_begin(ctx.h, n, float(R), _P(_dptr(r)), _P(_dptr(phi)), _P(_dptr(row_off)), col_in, k,
+                                 _P(_dptr(ids)) if k else _P(None), _P(_dptr(r_new)) if k else _P(None),
+                                 _P(_dptr(phi_new)) if k else _P(None), HRG_FLAG_FP64_ONLY if fp64_only else 0,
+                                 int(bands), _P(st.cuda_stream), _P(_dptr(off)), ctypes.byref(job), ctypes.byref(ne)))
     try:
         col = torch.empty(max(ne.value, 1), dtype=torch.int32, device=dev)
         ctx.check(L.hrg_generate_finish(job, _P(_dptr(col))))

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libhrg.so")
 SOURCES = ["hrg_points.cu", "hrg_query.cu", "hrg_sort.cu", "hrg_api.cu", "hrg_noalloc.cu", "hrg_server.cu",
-           "hrg_props.cu", "hrg_longrange.cu", "hrg_bfs.cu"]
+           "hrg_props.cu", "hrg_longrange.cu", "hrg_bfs.cu", "hrg_update.cu"]
 HEADERS = ["hrg_common.cuh", "hrg_internal.h", "hrg_graph_ops.h", "hrg_graph_util.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

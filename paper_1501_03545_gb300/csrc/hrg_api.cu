@@ -103,6 +103,16 @@ struct hrg_job {
     QueryBufs qb{};
     int32_t batch = 0;       // graphs of a batch job (0: a single graph)
     int64_t batch_G = 0;     // buckets over all graphs of a batch
+    // vertex movement (hrg_update_begin): the old CSR, the moves and the
+    // per-vertex bookkeeping between the two passes
+    bool update = false;
+    const int64_t *old_off = nullptr;
+    const int32_t *old_col = nullptr;
+    int64_t moves = 0;
+    const int32_t *move_ids = nullptr;
+    uint32_t *moved = nullptr;
+    int32_t *rem = nullptr, *gain = nullptr, *gain_cur = nullptr, *keep = nullptr;
+    int32_t compact_rows = 0;
 };
 
 struct hrg_ctx {
@@ -115,7 +125,7 @@ struct hrg_ctx {
            W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_POSOF, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
            W_PACC, W_POUTDEG, W_POUTOFF, W_POUTCOL, W_PTRI, W_PSCAN, W_LRCNT, W_LROFF, W_LRLIST, W_LRFIN,
            W_LRDEG, W_HPOOL, W_HRUNS, W_HPCUR, W_BFSF0, W_BFSF1, W_BFSDEG, W_BFSOFF, W_BFSACC, W_BFSDIST,
-           W_COUNT };
+           W_MVBITS, W_MVREM, W_MVADD, W_MVCUR, W_MVKEEP, W_MVERR, W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
     cudaEvent_t ev[10] = {};  // stage boundaries of the current job
@@ -474,7 +484,8 @@ static void expected_band_counts(const Plan &p, int64_t *cnt)
 
 static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params *prm, int64_t n, double R,
                         double alpha, const double *r_in, const double *phi_in, double *r_out, double *phi_out,
-                        uint32_t flags, int32_t bands, cudaStream_t st, int64_t *row_off_out, int64_t *n_entries)
+                        uint32_t flags, int32_t bands, cudaStream_t st, int64_t *row_off_out, int64_t *n_entries,
+                        bool count_pass = true)
 {
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
     J = hrg_job();
@@ -564,6 +575,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     b.pms64 = (PMS64 *)pms64;
     b.start = (int32_t *)start;
     b.pos_of = (int32_t *)pos_of;
+    if (!count_pass) return HRG_OK;  // the band structure only (vertex movement)
     return count_and_offsets(ctx, J, n, st, row_off_out, n_entries);
 }
 
@@ -793,6 +805,177 @@ extern "C" int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_p
     return HRG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Vertex movement (kernels in hrg_update.cu and hrg_query.cu).  Begin: the
+// moves checked and applied, the band structure rebuilt from the updated
+// points, the moved vertices counted, the removals and gains of the other
+// rows counted, new degrees and row offsets.  Finish (update_finish): the
+// rows written and the rows written out of order sorted.
+// ---------------------------------------------------------------------------
+static void job_stage_times(hrg_ctx *ctx, hrg_job *job)
+{
+    const int pairs[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {6, 7}, {7, 8}, {8, 9}};
+    for (int k = 0; k < 8; ++k) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[pairs[k][0]], ctx->ev[pairs[k][1]]) != cudaSuccess) {
+            cudaGetLastError();
+            ms = -1.0f;
+        }
+        job->stage_ms[k] = ms;
+    }
+}
+
+extern "C" int hrg_update_begin(hrg_ctx *ctx, int64_t n, double R, double *r, double *phi, const int64_t *row_off,
+                                const int32_t *col_idx, int64_t k, const int32_t *ids, const double *r_new,
+                                const double *phi_new, uint32_t flags, int32_t bands, void *stream,
+                                int64_t *row_off_out, hrg_job **job, int64_t *n_entries)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (!r || !phi || !row_off || !row_off_out || !job || !n_entries) return set_err(ctx, HRG_EINVAL, "null argument");
+    if (n < 1 || n > 0x7fffffffLL) return set_err(ctx, HRG_EINVAL, "n must be in [1, 2^31)");
+    if (k < 0 || k > n) return set_err(ctx, HRG_EINVAL, "k must be in [0, n]");
+    if (k > 0 && (!ids || !r_new || !phi_new)) return set_err(ctx, HRG_EINVAL, "null move arrays");
+    if (!(R > 0.0) || !std::isfinite(R)) return set_err(ctx, HRG_EINVAL, "R must be positive and finite");
+    if (bands < 0 || bands > HRG_MAX_BANDS) return set_err(ctx, HRG_EINVAL, "bands must be in [0, 64]");
+    if (ctx->job.open) return set_err(ctx, HRG_ESTATE, "a job of this context is still open");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *hp = (char *)ctx->pinned;
+    CK(cudaMemcpyAsync(hp, row_off, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 8, row_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int64_t o0, on;
+    memcpy(&o0, hp, 8);
+    memcpy(&on, hp + 8, 8);
+    if (on > o0 && !col_idx) return set_err(ctx, HRG_EINVAL, "null col_idx");
+
+    void *moved, *rem, *gain, *cur, *keep, *err;
+    int rc;
+    const int64_t words = (n + 31) / 32;
+    if ((rc = ensure(ctx, hrg_ctx::W_MVBITS, sizeof(uint32_t) * words, &moved))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_MVREM, sizeof(int32_t) * n, &rem))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_MVADD, sizeof(int32_t) * n, &gain))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_MVCUR, sizeof(int32_t) * n, &cur))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_MVKEEP, sizeof(int32_t) * n, &keep))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_MVERR, 64, &err))) return rc;
+    CK(cudaMemsetAsync(moved, 0, sizeof(uint32_t) * words, st));
+    CK(cudaMemsetAsync(err, 0, 64, st));
+    // 0. the moves: checked first, so that the points stay as they were on an error
+    CK(launch_move_check(n, k, R, ids, r_new, phi_new, (uint32_t *)moved, (int *)err, st));
+    CK(cudaMemcpyAsync(hp, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int bad;
+    memcpy(&bad, hp, 4);
+    if (bad & 1) return set_err(ctx, HRG_EINVAL, "a moved id outside [0, n) or a coordinate outside [0, R) x [0, 2pi)");
+    if (bad & 2) return set_err(ctx, HRG_EINVAL, "a vertex is moved twice");
+    CK(launch_move_apply(k, ids, r_new, phi_new, r, phi, st));
+
+    // 1-2. the band structure of the updated points
+    hrg_job &J = ctx->job;
+    rc = begin_common(ctx, J, false, nullptr, n, R, 1.0, r, phi, nullptr, nullptr, flags, bands, st, row_off_out,
+                      n_entries, false);
+    if (rc) {
+        J.open = false;
+        return rc;
+    }
+    J.update = true;
+    J.old_off = row_off;
+    J.old_col = col_idx;
+    J.moves = k;
+    J.move_ids = ids;
+    J.moved = (uint32_t *)moved;
+    J.rem = (int32_t *)rem;
+    J.gain = (int32_t *)gain;
+    J.gain_cur = (int32_t *)cur;
+    J.keep = (int32_t *)keep;
+
+    // 3. counts: the moved rows, the gains and the removals of the others
+    QueryBufs &b = J.qb;
+    void *deg, *stats, *lists[3], *listcnt, *bigtot, *scanws, *compact;
+    if ((rc = ensure(ctx, hrg_ctx::W_DEG, sizeof(int32_t) * n, &deg))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_STATS, sizeof(uint64_t) * 8, &stats))) return rc;
+    for (int c = 0; c < 3; ++c)
+        if ((rc = ensure(ctx, hrg_ctx::W_LIST0 + c, sizeof(int32_t) * n, &lists[c]))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 16, &listcnt))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_BIGTOT, sizeof(int64_t), &bigtot))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_RELIST0, sizeof(int32_t) * n, &compact))) return rc;
+    if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_workspace_bytes(n), &scanws))) return rc;
+    b.r = r;
+    b.phi = phi;
+    b.deg = (int32_t *)deg;
+    b.stats = (unsigned long long *)stats;
+    for (int c = 0; c < 3; ++c) b.rows[c] = (int32_t *)lists[c];
+    b.list_cnt = (int32_t *)listcnt;
+    b.big_total = (int64_t *)bigtot;
+    b.relist[0] = (int32_t *)compact;
+    CK(cudaMemsetAsync(stats, 0, sizeof(uint64_t) * 8, st));
+    CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 16, st));
+    CK(cudaMemsetAsync(bigtot, 0, sizeof(int64_t), st));
+    CK(cudaMemsetAsync(rem, 0, sizeof(int32_t) * n, st));
+    CK(cudaMemsetAsync(gain, 0, sizeof(int32_t) * n, st));
+    const Plan &p = J.plan;
+    CK(launch_move_query(p, b, J.fp64, false, k, ids, (uint32_t *)moved, (int32_t *)deg, (int32_t *)gain, nullptr,
+                         nullptr, nullptr, st));
+    CK(cudaEventRecord(ctx->ev[3], st));
+    CK(launch_move_removed(k, ids, row_off, col_idx, (uint32_t *)moved, (int32_t *)rem, st));
+    MoveLists ml{{(int32_t *)lists[0], (int32_t *)lists[1], (int32_t *)lists[2], (int32_t *)compact}};
+    CK(launch_move_degrees(n, row_off, (uint32_t *)moved, (int32_t *)rem, (int32_t *)gain, (int32_t *)deg,
+                           (int32_t *)keep, ml, (int32_t *)listcnt, (unsigned long long *)bigtot, st));
+    CK(cudaEventRecord(ctx->ev[4], st));
+    // 4. row offsets
+    CK(scan_i32_to_i64((int32_t *)deg, row_off_out, n, scanws, st));
+    CK(cudaEventRecord(ctx->ev[5], st));
+    CK(cudaMemcpyAsync(hp + 0, row_off_out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 8, listcnt, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 24, bigtot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hp + 64, stats, sizeof(uint64_t) * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    memcpy(&J.n_entries, hp + 0, 8);
+    memcpy(J.lists, hp + 8, 12);
+    memcpy(&J.compact_rows, hp + 20, 4);
+    memcpy(&J.big_total, hp + 24, 8);
+    memcpy(J.stats, hp + 64, 64);
+    J.open = true;
+    *n_entries = J.n_entries;
+    *job = &J;
+    return HRG_OK;
+}
+
+static int update_finish(hrg_job *job, int32_t *col_out)
+{
+    hrg_ctx *ctx = job->ctx;
+    cudaStream_t st = job->stream;
+    const Plan &p = job->plan;
+    const int64_t n = p.n;
+    CK(cudaEventRecord(ctx->ev[6], st));
+    CK(cudaMemsetAsync(job->gain_cur, 0, sizeof(int32_t) * n, st));
+    CK(launch_move_query(p, job->qb, job->fp64, true, job->moves, job->move_ids, job->moved, nullptr, job->gain_cur,
+                         job->keep, job->row_off, col_out, st));
+    CK(cudaEventRecord(ctx->ev[7], st));
+    CK(launch_move_rows(n, job->old_off, job->old_col, job->moved, job->rem, job->qb.relist[0],
+                        job->qb.list_cnt + 3, job->compact_rows, job->row_off, col_out, st));
+    CK(cudaEventRecord(ctx->ev[8], st));
+    if (job->lists[0] > 0 || job->lists[1] > 0 || job->lists[2] > 0) {
+        void *tmp = nullptr, *bws = nullptr;
+        int rc;
+        if (job->lists[2] > 0) {
+            if ((rc = ensure(ctx, hrg_ctx::W_TMP, sizeof(int32_t) * job->big_total, &tmp))) return rc;
+            if ((rc = ensure(ctx, hrg_ctx::W_BUCKET, big_sort_ws_bytes(job->lists[2], job->big_total), &bws)))
+                return rc;
+        }
+        CK(launch_sort_rows(p, job->qb, job->lists, job->big_total, job->row_off, col_out, (int32_t *)tmp, bws, st));
+    }
+    CK(cudaEventRecord(ctx->ev[9], st));
+    CK(launch_move_check_gains(n, job->gain, job->gain_cur, job->qb.stats + 7, st));
+    uint64_t *hs = (uint64_t *)ctx->pinned;
+    CK(cudaMemcpyAsync(hs, job->qb.stats + 7, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    job->finished = true;
+    job_stage_times(ctx, job);
+    if (hs[0] != 0) return set_err(ctx, HRG_EINTERNAL, "count and write passes of the update disagree");
+    return HRG_OK;
+}
+
 extern "C" int hrg_generate_finish(hrg_job *job, int32_t *col_idx_out)
 {
     if (!job || !job->ctx) return HRG_EINVAL;
@@ -800,6 +983,7 @@ extern "C" int hrg_generate_finish(hrg_job *job, int32_t *col_idx_out)
     if (!job->open || job->finished) return set_err(ctx, HRG_ESTATE, "job is not open");
     if (!col_idx_out && job->n_entries > 0) return set_err(ctx, HRG_EINVAL, "null col_idx");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    if (job->update) return update_finish(job, col_idx_out);
     cudaStream_t st = job->stream;
     const Plan &p = job->plan;
     CK(cudaEventRecord(ctx->ev[6], st));
@@ -860,6 +1044,21 @@ extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
     out->rows_no_room = (int64_t)job->stats[4];
     out->hub_rows_retraversed = (job->p_hub > 0 && !job->hub_pooled) ? job->p_hub : 0;
     out->heavy_retries = job->heavy_retries;
+    if (job->update) {
+        // check, apply, band counts, bucket histogram, bucket scan, scatter
+        // (records + split, 2; the FP64 path 1), moved count, removals,
+        // degrees, row-offset scan; write: moved rows, flat copy (+ compaction),
+        // row sorts, gain check
+        const int scatter = job->fp64 ? 1 : 2;
+        int L = (job->moves > 0 ? 2 : 0) + 2 + scan_launches(job->plan.G) + scatter + (job->moves > 0 ? 2 : 0) + 1 +
+                scan_launches(job->plan.n);
+        if (job->finished)
+            L += (job->moves > 0 ? 1 : 0) + 1 + (job->compact_rows > 0 ? 1 : 0) + sort_launches(job->lists) + 1;
+        out->launches = L;
+        out->hub_rows_retraversed = 0;
+        out->hub_queries = 0;
+        return HRG_OK;
+    }
     // kernels launched: points with their buckets (1; an injected point set:
     // band counts + bucket histogram, 2), bucket scan, structure-of-arrays
     // scatter (records + split, 2; the FP64 path 1), count (hub 3, rim 1),

@@ -182,6 +182,38 @@ cudaError_t launch_write_hub(const Plan &p, const QueryBufs &b, bool fp64_only, 
 cudaError_t launch_write_rim(const Plan &p, const QueryBufs &b, bool fp64_only, const int64_t *row_off,
                              int32_t *col_idx, cudaStream_t s);
 int query_launches(const Plan &p, int32_t p_hub, bool write);
+// Moved vertices of a dynamic update: one CTA per id in ids[k] queries its
+// position in the band structure.  Count (write = false): deg[u] = new
+// degree, add[w] += 1 for each neighbour w whose bit in moved is clear.
+// Write: u's row (unsorted) at row_off_out[u]; u into each such w's row at
+// row_off_out[w] + keep[w] + (slot from add[w], zeroed by the caller).
+cudaError_t launch_move_query(const Plan &p, const QueryBufs &b, bool fp64_only, bool write, int64_t k,
+                              const int32_t *ids, const uint32_t *moved, int32_t *deg, int32_t *add,
+                              const int32_t *keep, const int64_t *row_off_out, int32_t *col_out, cudaStream_t s);
+
+// ---- vertex movement (hrg_update.cu) ----
+// moved: one bit per vertex (zeroed by the caller); err |= 1 for an id or a
+// coordinate out of range, 2 for a repeated id.
+cudaError_t launch_move_check(int64_t n, int64_t k, double R, const int32_t *ids, const double *r_new,
+                              const double *phi_new, uint32_t *moved, int *err, cudaStream_t s);
+cudaError_t launch_move_apply(int64_t k, const int32_t *ids, const double *r_new, const double *phi_new, double *r,
+                              double *phi, cudaStream_t s);
+// rem[w] += moved vertices in the old row of w (w not moved; rem zeroed by the caller)
+cudaError_t launch_move_removed(int64_t k, const int32_t *ids, const int64_t *row_off, const int32_t *col_idx,
+                                const uint32_t *moved, int32_t *rem, cudaStream_t s);
+// new degrees (deg: moved rows' counts in, all new degrees out), keep[w] =
+// old degree - removed; l[3]: rows to compact, l[0..2]: rows to sort by
+// length class as for the row sort (counts cnt[0..3] zeroed by the caller)
+struct MoveLists { int32_t *l[4]; };
+cudaError_t launch_move_degrees(int64_t n, const int64_t *row_off, const uint32_t *moved, const int32_t *rem,
+                                const int32_t *add, int32_t *deg, int32_t *keep, MoveLists lists, int32_t *cnt,
+                                unsigned long long *big_total, cudaStream_t s);
+// the rows of vertices that stay: untouched ones copied flat, the ones that lost entries compacted
+cudaError_t launch_move_rows(int64_t n, const int64_t *row_off, const int32_t *col_idx, const uint32_t *moved,
+                             const int32_t *rem, const int32_t *compact_rows, const int32_t *n_compact,
+                             int32_t compact_count, const int64_t *row_off_out, int32_t *col_out, cudaStream_t s);
+cudaError_t launch_move_check_gains(int64_t n, const int32_t *cnt, const int32_t *cur, unsigned long long *err,
+                                    cudaStream_t s);
 
 // Sort rows longer than kRegRow; tmp holds big_total ids, ws big_sort_ws_bytes.
 size_t sort_smem_bytes();

@@ -21,6 +21,7 @@
 //   * hub bands (few vertices, wide windows): one warp per query; lane j
 //     sets up band j's window, then all lanes stride over each band's
 //     candidates.
+#include <algorithm>
 #include <cstdio>
 #include "hrg_internal.h"
 
@@ -77,10 +78,11 @@ __device__ __forceinline__ bool within(uint64_t Aq, uint64_t Ac, uint64_t W)
 // pairs of the tie band (each pair once: from its smaller id); one counter
 // keeps the register budget of the hot loop.
 constexpr unsigned kTieUnit = 1u << 24;
+// tie_side: whether this side of the pair counts it (one of the two sides).
 template <bool F64>
-__device__ __forceinline__ bool decide_loaded(const Plan &p, const QueryBufs &b, const PMS &q, const PMS64 &q64,
-                                              uint64_t Aq, uint64_t Ac, const PMS &cc, int32_t cpos, uint64_t W,
-                                              unsigned &n_cand, unsigned &n_re)
+__device__ __forceinline__ bool decide_pair(const Plan &p, const QueryBufs &b, const PMS &q, const PMS64 &q64,
+                                            uint64_t Aq, uint64_t Ac, const PMS &cc, int32_t cpos, uint64_t W,
+                                            unsigned &n_cand, unsigned &n_re, bool tie_side)
 {
     if (W != kFullCircle && !within(Aq, Ac, W)) return false;
     ++n_cand;
@@ -88,16 +90,25 @@ __device__ __forceinline__ bool decide_loaded(const Plan &p, const QueryBufs &b,
         const PMS64 c64 = b.pms64[cpos];
         const double v = lhs_pms64(q64, c64);
         const long long vb = __double_as_longlong(v);
-        if (vb > p.tie_lo && vb < p.tie_hi && q.id < cc.id) n_re += kTieUnit;
+        if (vb > p.tie_lo && vb < p.tie_hi && tie_side) n_re += kTieUnit;
         return v < p.rhs64;
     } else {
         const float v = lhs32(q, cc, (int64_t)(Ac - Aq));
         if (v < p.rhs32 * (1.0f - p.mu)) return true;
         if (v > p.rhs32 * (1.0f + p.mu)) return false;
         const double d = cosh_dist64(__ldg(b.r + q.id), __ldg(b.phi + q.id), __ldg(b.r + cc.id), __ldg(b.phi + cc.id));
-        n_re += 1u + ((fabs(d - p.coshR) < kTieBand * p.coshR && q.id < cc.id) ? kTieUnit : 0u);
+        n_re += 1u + ((fabs(d - p.coshR) < kTieBand * p.coshR && tie_side) ? kTieUnit : 0u);
         return d < p.coshR;
     }
+}
+
+// every vertex queries: the pair counts from its smaller id
+template <bool F64>
+__device__ __forceinline__ bool decide_loaded(const Plan &p, const QueryBufs &b, const PMS &q, const PMS64 &q64,
+                                              uint64_t Aq, uint64_t Ac, const PMS &cc, int32_t cpos, uint64_t W,
+                                              unsigned &n_cand, unsigned &n_re)
+{
+    return decide_pair<F64>(p, b, q, q64, Aq, Ac, cc, cpos, W, n_cand, n_re, q.id < cc.id);
 }
 
 __device__ __forceinline__ void add_stats(unsigned long long *stats, unsigned n_cand, unsigned n_re, unsigned n_edge)
@@ -902,6 +913,104 @@ static void rim_write_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only
     }
 }
 
+// ---------------------------------------------------------------------------
+// Moved vertices of a dynamic update (hrg_update_begin): one CTA per moved
+// vertex u queries its new position against the rebuilt band structure (all
+// points at their current coordinates), every thread striding over each
+// band's window.  Count pass: u's new degree into deg[u], and add[w] += 1 for
+// every neighbour w that did not move (w gains u).  Write pass: u's row,
+// unsorted, at row_off_out[u], and u itself into each such w's row after
+// w's kept entries (keep[w]) at the slot add[w] hands out.  moved is a bit
+// per vertex.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool moved_bit(const uint32_t *__restrict__ moved, int32_t v)
+{
+    return (__ldg(moved + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+template <bool F64, bool WRITE>
+__global__ void __launch_bounds__(256) k_move_query(Plan p, QueryBufs b, int64_t k, const int32_t *__restrict__ ids,
+                                                    const uint32_t *__restrict__ moved, int32_t *__restrict__ deg,
+                                                    int32_t *__restrict__ add, const int32_t *__restrict__ keep,
+                                                    const int64_t *__restrict__ row_off_out, int32_t *col_out)
+{
+    __shared__ int32_t s_cnt;
+    __shared__ int32_t s_red[8];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned n_cand = 0, n_re = 0, n_edge = 0;
+    for (int64_t i = blockIdx.x; i < k; i += gridDim.x) {
+        const int32_t u = __ldg(ids + i);
+        const int32_t qp = __ldg(b.pos_of + u);
+        const PMS q = b.pms[qp];
+        const uint64_t Aq = b.A[qp];
+        PMS64 q64{};
+        if (F64) q64 = b.pms64[qp];
+        int64_t base = 0;
+        if (WRITE) base = row_off_out[u];
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        int32_t mine = 0;
+        for (int j = p.first_band; j < p.B; ++j) {
+            const Ranges rg = band_ranges(p, b.start, q, Aq, j);
+            for (int part = 0; part < 2; ++part) {
+                const int32_t s = part ? rg.s1 : rg.s0, e = part ? rg.e1 : rg.e0;
+                for (int32_t c0 = s; c0 < e; c0 += blockDim.x) {  // uniform trip count per warp
+                    const int32_t c = c0 + (int32_t)threadIdx.x;
+                    const bool v = c < e && c != qp;
+                    uint64_t Ac = 0;
+                    PMS pc{};
+                    bool other_moved = false;
+                    if (v) {
+                        Ac = __ldg(b.A + c);
+                        pc = b.pms[c];
+                        other_moved = moved_bit(moved, pc.id);
+                    }
+                    // a pair with a vertex that stays is queried from this side only
+                    const bool ed = v && decide_pair<F64>(p, b, q, q64, Aq, Ac, pc, c, rg.W, n_cand, n_re,
+                                                          !other_moved || u < pc.id);
+                    const bool stays = ed && !other_moved;
+                    if (!WRITE) {
+                        mine += (int)ed;
+                        if (stays) atomicAdd(add + pc.id, 1);
+                    } else {
+                        const unsigned m = __ballot_sync(0xffffffffu, ed);
+                        if (m) {
+                            int32_t off = 0;
+                            if (lane == 0) off = atomicAdd(&s_cnt, __popc(m));
+                            off = __shfl_sync(0xffffffffu, off, 0) + __popc(m & lt);
+                            if (ed) col_out[base + off] = pc.id;
+                        }
+                        if (stays) {
+                            const int32_t w = pc.id;
+                            col_out[row_off_out[w] + __ldg(keep + w) + atomicAdd(add + w, 1)] = u;
+                        }
+                    }
+                }
+            }
+        }
+        if (!WRITE) {
+            int32_t d = mine;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if (lane == 0) s_red[threadIdx.x >> 5] = d;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int32_t t = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
+                deg[u] = t;
+                n_edge += t;
+            }
+        } else {
+            __syncthreads();
+            if (threadIdx.x == 0 && (int64_t)s_cnt != row_off_out[u + 1] - base)
+                atomicOr((unsigned long long *)&b.stats[ST_ERR], 1ull);
+        }
+        __syncthreads();
+    }
+    if (!WRITE) add_stats(b.stats, n_cand, n_re, n_edge);
+}
+
 }  // namespace
 
 int query_launches(const Plan &p, int32_t p_hub, bool write)
@@ -934,6 +1043,22 @@ cudaError_t launch_write_hub(const Plan &p, const QueryBufs &b, bool fp64_only, 
     bw.col_out = col_idx;
     hub_dispatch<true>(p, bw, fp64_only, p_hub, row_off, s);
     k_hub_check<<<(unsigned)((p_hub + 255) / 256), 256, 0, s>>>(bw, p_hub);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_move_query(const Plan &p, const QueryBufs &b, bool fp64_only, bool write, int64_t k,
+                              const int32_t *ids, const uint32_t *moved, int32_t *deg, int32_t *add,
+                              const int32_t *keep, const int64_t *row_off_out, int32_t *col_out, cudaStream_t s)
+{
+    if (k <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)std::min<int64_t>(k, 152 * 8);
+    if (fp64_only) {
+        if (write) k_move_query<true, true><<<g, 256, 0, s>>>(p, b, k, ids, moved, deg, add, keep, row_off_out, col_out);
+        else k_move_query<true, false><<<g, 256, 0, s>>>(p, b, k, ids, moved, deg, add, keep, row_off_out, col_out);
+    } else {
+        if (write) k_move_query<false, true><<<g, 256, 0, s>>>(p, b, k, ids, moved, deg, add, keep, row_off_out, col_out);
+        else k_move_query<false, false><<<g, 256, 0, s>>>(p, b, k, ids, moved, deg, add, keep, row_off_out, col_out);
+    }
     return cudaGetLastError();
 }
 

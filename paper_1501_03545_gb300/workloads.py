@@ -14,6 +14,9 @@ is measured and checked on:
 * ``LARGE``    n = 1e8,  alpha = 0.55 (gamma = 2.1), kbar = 16, seed 3
 * ``EXAMPLE``  n = 500,  alpha = 0.8, R = 5.08 -- the illustrative graph of
   Sec. 2.1 (its R is printed, its kbar is not).
+
+``moves`` draws the vertex movements that the dynamic update takes as input
+(the paper defines no movement law).
 """
 from __future__ import annotations
 
@@ -111,3 +114,34 @@ def serving_requests(count: int, rate: float = SERVE_RATE, draw_seed: int = SERV
     alpha = g.uniform(0.55, 1.5, size=count)
     kbar = g.uniform(4.0, 32.0, size=count)
     return [(float(t[k]), int(n[k]), float(alpha[k]), float(kbar[k]), first_seed + k) for k in range(count)]
+
+
+# ---------------------------------------------------------------------------
+# Vertex movement: the paper leaves the law of motion open, so the moves of a
+# dynamic update are synthetic inputs.
+# ---------------------------------------------------------------------------
+def moves(r, phi, R: float, k: int, seed: int):
+    """k distinct vertices and their new coordinates, from the current points
+    (numpy arrays r, phi) and numpy's generator seeded with ``seed``: 60 %
+    small steps (r + N(0, 0.3), phi + N(0, 1e-3)), 10 % to just beside
+    phi = 0 on either side (through the wrap point), 15 % to a radius
+    uniform on [0, R) (across bands, some to the centre), 15 % to the rim
+    (R - Exp(1)).  Returns (ids int32, r_new, phi_new) with 0 <= r_new < R
+    and 0 <= phi_new < 2 pi."""
+    g = np.random.default_rng(seed)
+    n = len(r)
+    ids = np.sort(g.choice(n, size=k, replace=False)).astype(np.int32)
+    kind = g.uniform(size=k)
+    r0, p0 = np.asarray(r, dtype=np.float64)[ids], np.asarray(phi, dtype=np.float64)[ids]
+    rn = r0 + g.normal(0.0, 0.3, size=k)
+    pn = p0 + g.normal(0.0, 1e-3, size=k)
+    wrap = (kind >= 0.60) & (kind < 0.70)
+    pn = np.where(wrap, g.normal(0.0, 1e-4, size=k), pn)
+    jump = (kind >= 0.70) & (kind < 0.85)
+    rn = np.where(jump, g.uniform(0.0, R, size=k), rn)
+    rim = kind >= 0.85
+    rn = np.where(rim, R - g.exponential(1.0, size=k), rn)
+    rn = np.clip(rn, 0.0, np.nextafter(R, 0.0))
+    pn = np.mod(pn, 2.0 * np.pi)
+    pn = np.where(pn >= 2.0 * np.pi, 0.0, pn)
+    return ids, rn.astype(np.float64), pn.astype(np.float64)
