@@ -359,25 +359,4 @@ __device__ __forceinline__ uint64_t window_halfwidth(const Plan &p, const PMS &q
     return float_to_u64_ru(th * kAngleScaleUp) + (1ull << 16);
 }
 
-// An upper bound of window_halfwidth over every query whose radius is at
-// least that of q (q at the inner radius of a band beyond `band`): the window
-// shrinks as the query moves out (r_q >= b), X carries an extra 1e-4 relative
-// pad against the FP32 rounding of the two queries' data, and
-// 2 sqrt(X / (1 - X)) >= 2 asin(sqrt X) bounds both of window_halfwidth's
-// branches.
-__device__ __forceinline__ uint64_t window_bound(const Plan &p, const PMS &q, int band)
-{
-    const float Pb = p.Pb[band], Mb = p.Mb[band], Sb = p.Sb[band];
-    const float den = q.S * Sb;
-    if (!(den > 0.0f)) return kFullCircle;
-    const float sub = fmaf(q.P, Mb, Pb * q.M);
-    const float num = p.rhs32 - sub;
-    float X = fmaf(num, 1.0f + 2e-5f, 2e-5f * (1.0f + sub)) / den * (1.0f + 1e-4f);
-    if (X >= 0.999f) return kFullCircle;
-    if (!(X > 0.0f)) X = 0.0f;
-    const float th = 2.0f * sqrtf(X / (1.0f - X)) * (1.0f + 1e-3f) + 1e-30f;
-    if (th >= 3.1415f) return kFullCircle;
-    return float_to_u64_ru(th * kAngleScaleUp) + (1ull << 20);
-}
-
 }  // namespace hrg

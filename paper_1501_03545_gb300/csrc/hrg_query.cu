@@ -66,6 +66,49 @@ __device__ __forceinline__ Ranges band_ranges(const Plan &p, const int32_t *__re
     return rg;
 }
 
+// Candidate positions in band j of every query whose fixed-point angle lies
+// in [Amin, Amax] (no wrap: one angular sector) and whose window is at most
+// W: the buckets of [Amin - W, Amax + W], one or two ranges, or the whole
+// band.
+__device__ __forceinline__ Ranges span_ranges(const Plan &p, const int32_t *__restrict__ start, uint64_t Amin,
+                                              uint64_t Amax, uint64_t W, int j)
+{
+    Ranges rg;
+    const int64_t b0 = p.base[j];
+    const int g = p.gbits[j];
+    const int64_t G = (int64_t)1 << g;
+    rg.W = W;
+    int64_t i0 = 0, i1 = G, i2 = 0, i3 = 0;
+    const uint64_t span = Amax - Amin;
+    if (W != kFullCircle && g != 0 && W < (~0ull - span) / 2) {
+        const uint64_t lo = Amin - W, hi = Amax + W;
+        const int64_t bl = (int64_t)(lo >> (64 - g)), bh = (int64_t)(hi >> (64 - g));
+        if (lo <= hi) {
+            i0 = bl;
+            i1 = bh + 1;
+        } else if (bh < bl) {  // through angle 0
+            i0 = bl;
+            i3 = bh + 1;
+        }  // else the gap lies inside one bucket: the whole band
+    }
+    rg.s0 = __ldg(start + b0 + i0);
+    rg.e0 = __ldg(start + b0 + i1);
+    rg.s1 = __ldg(start + b0 + i2);
+    rg.e1 = __ldg(start + b0 + i3);
+    return rg;
+}
+
+__device__ __forceinline__ Ranges shfl_ranges(const Ranges &r, int src)
+{
+    Ranges o;
+    o.s0 = __shfl_sync(0xffffffffu, r.s0, src);
+    o.e0 = __shfl_sync(0xffffffffu, r.e0, src);
+    o.s1 = __shfl_sync(0xffffffffu, r.s1, src);
+    o.e1 = __shfl_sync(0xffffffffu, r.e1, src);
+    o.W = __shfl_sync(0xffffffffu, r.W, src);
+    return o;
+}
+
 __device__ __forceinline__ bool within(uint64_t Aq, uint64_t Ac, uint64_t W)
 {
     const uint64_t d = Ac - Aq;
@@ -170,6 +213,8 @@ __device__ __forceinline__ void warp_append(int32_t *list, int32_t *count, bool 
     if (e) list[base + __popc(m & ((1u << lane) - 1u))] = v;
 }
 
+constexpr int kRimThreads = 256;
+
 // ---------------------------------------------------------------------------
 // One query, one thread (rim bands).  The count pass stores a row of up to
 // kKeepRow entries in the row buffer (b.small) and records where
@@ -180,13 +225,13 @@ __device__ __forceinline__ void warp_append(int32_t *list, int32_t *count, bool 
 // by the write pass, which keeps rows of up to kRegRow entries sorted in
 // registers.
 // ---------------------------------------------------------------------------
-// The traversal.  Count pass: every query of the sector; write pass: only
-// queries whose row was not kept (no warp-collective operations there, so
-// the write pass may call it for any subset of lanes).  hub_mask clears the
-// bands that hold no point within reach of the query (count pass).
+// The traversal.  Count pass: every query of the sector, all lanes of the
+// warp together (warp-collective operations); write pass: only queries whose
+// row was not kept (no warp-collective operations there, so the write pass
+// may call it for any subset of lanes).
 template <bool F64, bool WRITE>
 __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, int32_t qp, bool active,
-                                             uint64_t hub_mask, const int64_t *__restrict__ row_off,
+                                             const int64_t *__restrict__ row_off,
                                              int32_t *__restrict__ col_idx, unsigned &n_cand, unsigned &n_re,
                                              unsigned &n_edge)
 {
@@ -203,12 +248,96 @@ __device__ __forceinline__ void thread_query(const Plan &p, const QueryBufs &b, 
     }
     int32_t buf[kKeepRow];
     int32_t cnt = 0;
+    if (!WRITE) {
+        // Count pass (all lanes of the warp here): the hub bands for the
+        // warp's queries together.  Their windows shrink as the query moves
+        // out, so the window at the warp's smallest radius, widened by the
+        // warp's angular span, holds every candidate of every lane; lane h
+        // finds band h's range, then all lanes walk each range (the same
+        // candidate for all lanes: one load) and decide it for their own
+        // query by the predicate alone.
+        const int H = p.hub_bands;
+        if (H > p.first_band && __any_sync(0xffffffffu, active)) {
+            const uint64_t Aq = active ? b.A[qp] : 0ull;
+            PMS64 q64{};
+            if (F64 && active) q64 = b.pms64[qp];
+            const unsigned pkey = active ? __float_as_uint(q.P) : 0xFFFFFFFFu;  // P > 0: bits order like values
+            const unsigned pmin = __reduce_min_sync(0xffffffffu, pkey);
+            const int src = __ffs(__ballot_sync(0xffffffffu, pkey == pmin)) - 1;
+            PMS qm;
+            qm.P = __shfl_sync(0xffffffffu, q.P, src);
+            qm.M = __shfl_sync(0xffffffffu, q.M, src);
+            qm.S = __shfl_sync(0xffffffffu, q.S, src);
+            qm.id = 0;
+            uint64_t amin = active ? Aq : ~0ull, amax = active ? Aq : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint64_t x = __shfl_xor_sync(0xffffffffu, amin, o), y = __shfl_xor_sync(0xffffffffu, amax, o);
+                amin = min(amin, x);
+                amax = max(amax, y);
+            }
+            for (int h0 = 0; h0 < H; h0 += 32) {
+                const int hl = h0 + lane;
+                Ranges mine{0, 0, 0, 0, 0};
+                if (hl < H && hl >= p.first_band)
+                    mine = span_ranges(p, b.start, amin, amax, window_halfwidth(p, qm, hl), hl);
+                // the candidates of all these bands as one list: lane h's
+                // ranges hold items [excl, incl) of it
+                const int32_t n0 = max(0, mine.e0 - mine.s0), nh = n0 + max(0, mine.e1 - mine.s1);
+                int32_t incl = nh;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                for (int32_t i0 = 0; i0 < total; i0 += 32) {
+                    // lane l loads item i0 + l: its band lane is the first with incl > item
+                    const int32_t it = i0 + lane;
+                    int own = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int32_t v = __shfl_sync(0xffffffffu, incl, own + step - 1);
+                        if (v <= it) own += step;
+                    }
+                    own = min(own, 31);
+                    const int32_t o_incl = __shfl_sync(0xffffffffu, incl, own);
+                    const int32_t o_n = __shfl_sync(0xffffffffu, nh, own);
+                    const int32_t o_n0 = __shfl_sync(0xffffffffu, n0, own);
+                    const int32_t o_s0 = __shfl_sync(0xffffffffu, mine.s0, own);
+                    const int32_t o_s1 = __shfl_sync(0xffffffffu, mine.s1, own);
+                    const int32_t pos = it - (o_incl - o_n);
+                    const int32_t cp = pos < o_n0 ? o_s0 + pos : o_s1 + (pos - o_n0);
+                    uint64_t Al = 0;
+                    PMS pl{};
+                    if (it < total) {
+                        Al = __ldg(b.A + cp);
+                        pl = b.pms[cp];
+                    }
+                    const int m = min(32, total - i0);
+                    for (int k = 0; k < m; ++k) {  // warp-uniform: every lane decides item i0 + k
+                        PMS cc;
+                        cc.P = __shfl_sync(0xffffffffu, pl.P, k);
+                        cc.M = __shfl_sync(0xffffffffu, pl.M, k);
+                        cc.S = __shfl_sync(0xffffffffu, pl.S, k);
+                        cc.id = __shfl_sync(0xffffffffu, pl.id, k);
+                        const uint64_t Ac = __shfl_sync(0xffffffffu, Al, k);
+                        const int32_t c = __shfl_sync(0xffffffffu, cp, k);
+                        if (!active) continue;
+                        if (!decide_loaded<F64>(p, b, q, q64, Aq, Ac, cc, c, kFullCircle, n_cand, n_re)) continue;
+                        if (cnt < kKeepRow) buf[cnt] = cc.id;
+                        ++cnt;
+                    }
+                }
+            }
+        }
+    }
     if (active) {
         const uint64_t Aq = b.A[qp];
         PMS64 q64{};
         if (F64) q64 = b.pms64[qp];
-        for (int j = p.first_band; j < p.B; ++j) {  // bands before first_band hold no point
-            if (j < 64 && !((hub_mask >> j) & 1ull)) continue;  // no point of band j within reach
+        // bands before first_band hold no point; the count pass has done the hub bands
+        for (int j = WRITE ? p.first_band : max(p.first_band, p.hub_bands); j < p.B; ++j) {
             const Ranges rg = band_ranges(p, b.start, q, Aq, j);
             for (int part = 0; part < 2; ++part) {
                 const int32_t s = part ? rg.s1 : rg.s0, e = part ? rg.e1 : rg.e0;
@@ -313,37 +442,7 @@ __device__ __forceinline__ void rim_sector(const Plan &p, const QueryBufs &b, in
         s_pre[0] = 0;
         for (int j = 0; j < HRG_MAX_BANDS; ++j) s_pre[j + 1] += s_pre[j];
     }
-    // Hub bands that the queries of a rim band of this sector can reach: the
-    // sector widened by a bound of their windows (window_bound at the rim
-    // band's inner radius).  A hub band with no point there is skipped by
-    // every query of that rim band.
-    __shared__ unsigned long long s_mask[HRG_MAX_BANDS];
-    const int H = p.hub_bands, NR = p.B - p.hub_bands;
-    for (int t = threadIdx.x; t < HRG_MAX_BANDS; t += blockDim.x) s_mask[t] = ~0ull;
     __syncthreads();
-    if (p.sbits > 0) {
-        for (int t = threadIdx.x; t < NR * H; t += blockDim.x) {
-            const int i = H + t / H, jh = t % H;
-            if (jh < p.first_band) continue;
-            const PMS qi = scaled_exps(p, p.band_lo[i], 0);
-            const uint64_t W = window_bound(p, qi, jh);
-            const int g = p.gbits[jh];
-            const uint64_t span = (1ull << (64 - p.sbits)) - 1;  // the sector is [slo, slo + span]
-            if (W == kFullCircle || g == 0 || W >= (~0ull - span) / 2) continue;
-            const uint64_t slo = (uint64_t)sector << (64 - p.sbits);
-            const uint64_t lo = slo - W, hi = slo + span + W;
-            const int64_t b0 = p.base[jh], G = (int64_t)1 << g;
-            const int64_t bl = (int64_t)(lo >> (64 - g)), bh = (int64_t)(hi >> (64 - g));
-            int32_t pts;
-            if (lo <= hi) pts = __ldg(b.start + b0 + bh + 1) - __ldg(b.start + b0 + bl);
-            else if (bh < bl)
-                pts = (__ldg(b.start + b0 + G) - __ldg(b.start + b0 + bl)) + (__ldg(b.start + b0 + bh + 1) -
-                                                                               __ldg(b.start + b0));
-            else continue;
-            if (pts == 0) atomicAnd(&s_mask[i], ~(1ull << jh));
-        }
-        __syncthreads();
-    }
     const int32_t total = s_pre[HRG_MAX_BANDS];
     unsigned n_cand = 0, n_re = 0, n_edge = 0;
     int j = 0;
@@ -356,8 +455,7 @@ __device__ __forceinline__ void rim_sector(const Plan &p, const QueryBufs &b, in
             while (t >= s_pre[j + 1]) ++j;  // t only grows, so j only moves forward
             qp = s_beg[j] + (t - s_pre[j]);
         }
-        thread_query<F64, false>(p, b, qp, active, active ? s_mask[j] : ~0ull, nullptr, nullptr, n_cand, n_re,
-                                 n_edge);
+        thread_query<F64, false>(p, b, qp, active, nullptr, nullptr, n_cand, n_re, n_edge);
     }
     add_stats(b.stats, n_cand, n_re, n_edge);
 }
@@ -472,10 +570,10 @@ __global__ void __launch_bounds__(256) k_rim_relist(Plan p, QueryBufs b, const i
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
         const int32_t qp = relist[k];
         if (BATCH)
-            thread_query<F64, true>(b.plans[__ldg(b.graph_of + qp)], b, qp, true, ~0ull, row_off, col_idx, n_cand,
-                                    n_re, n_edge);
+            thread_query<F64, true>(b.plans[__ldg(b.graph_of + qp)], b, qp, true, row_off, col_idx, n_cand, n_re,
+                                    n_edge);
         else
-            thread_query<F64, true>(p, b, qp, true, ~0ull, row_off, col_idx, n_cand, n_re, n_edge);
+            thread_query<F64, true>(p, b, qp, true, row_off, col_idx, n_cand, n_re, n_edge);
     }
 }
 
@@ -494,7 +592,7 @@ __device__ __forceinline__ int graph_search(const int64_t *__restrict__ off, int
 // sector x; the sector table gives its graph.  Four CTAs per SM leave 64
 // registers a thread, room for the candidate prefetch without spilling.
 template <bool F64, bool BATCH>
-__global__ void __launch_bounds__(256, 4) k_rim_sector(Plan p, QueryBufs b)
+__global__ void __launch_bounds__(kRimThreads, 4) k_rim_sector(Plan p, QueryBufs b)
 {
     if (BATCH) {
         const int g = graph_search(b.sec_off, b.NG, blockIdx.x);
@@ -544,16 +642,6 @@ __device__ __forceinline__ void pool_flush(const QueryBufs &b, int32_t qi, const
     off = __shfl_sync(0xffffffffu, off, 0);
     for (int32_t k = lane; k < fill; k += 32) b.pool[off + k] = buf[k];
     if (lane == 0) b.runs[run] = make_int4(qi, fill, (int)(uint32_t)off, (int)(uint32_t)(off >> 32));
-}
-__device__ __forceinline__ Ranges shfl_ranges(const Ranges &r, int src)
-{
-    Ranges o;
-    o.s0 = __shfl_sync(0xffffffffu, r.s0, src);
-    o.e0 = __shfl_sync(0xffffffffu, r.e0, src);
-    o.s1 = __shfl_sync(0xffffffffu, r.s1, src);
-    o.e1 = __shfl_sync(0xffffffffu, r.e1, src);
-    o.W = __shfl_sync(0xffffffffu, r.W, src);
-    return o;
 }
 
 // write of this lane's edge (if any) at the warp's running offset pos of a
@@ -889,11 +977,11 @@ static void rim_count_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only
 {
     const bool batch = b.plans != nullptr;
     if (fp64_only) {
-        if (batch) k_rim_sector<true, true><<<sectors, 256, 0, s>>>(p, b);
-        else k_rim_sector<true, false><<<sectors, 256, 0, s>>>(p, b);
+        if (batch) k_rim_sector<true, true><<<sectors, kRimThreads, 0, s>>>(p, b);
+        else k_rim_sector<true, false><<<sectors, kRimThreads, 0, s>>>(p, b);
     } else {
-        if (batch) k_rim_sector<false, true><<<sectors, 256, 0, s>>>(p, b);
-        else k_rim_sector<false, false><<<sectors, 256, 0, s>>>(p, b);
+        if (batch) k_rim_sector<false, true><<<sectors, kRimThreads, 0, s>>>(p, b);
+        else k_rim_sector<false, false><<<sectors, kRimThreads, 0, s>>>(p, b);
     }
 }
 
