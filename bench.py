@@ -344,8 +344,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--update-steps", type=int, default=3, help="timed updates per move count (vertex movement)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-slots", type=int, default=2)
     ap.add_argument("--oracle-n", type=int, default=ORACLE_SAMPLE_N)
@@ -434,8 +435,10 @@ def main():
             ne, _ = H.generate_host(ctx, n, w.alpha, w.kbar, seed, rh, ph, oh, ch)
             per.append(time.perf_counter() - t0)
         es = statistics.median(per)
+        srt = sorted(per)
         e2e = {"value": ne / es, "unit": UNIT, "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": int(16 * n + 8 * (n + 1) + 4 * ne), "ms_per_step": 1e3 * es,
+               "ms_min": 1e3 * srt[0], "ms_p90": 1e3 * srt[min(len(srt) - 1, int(0.9 * len(srt)))],
                "ms_steps": [round(1e3 * x, 1) for x in per], "statistic": "median over steps"}
         del rh, ph, oh, ch
 
@@ -455,6 +458,45 @@ def main():
         torch.cuda.synchronize()
         fms = a.elapsed_time(b) / args.fp64_steps
         fp64 = {"value": n_entries / (fms / 1e3), "unit": UNIT, "ms_per_step": fms}
+
+    # vertex movement on the timed graph: k vertices moved (hrg_update_begin),
+    # the update's device time against a full generation of the graph
+    dynamic = None
+    if args.update_steps > 0:
+        import numpy as np
+
+        g = step()
+        R = g["stats"]["R"]
+        r, phi, off, col = g["r"], g["phi"], g["row_off"], g["col_idx"]
+        del g
+        sel = torch.randint(0, w.n, (1 << 21,), generator=torch.Generator().manual_seed(5), device="cpu")
+        sel = torch.unique(sel)
+        dynamic = {"recipe": "moves of workloads.moves without radial jumps (75 % small steps, 10 % through phi = 0, "
+                             "15 % to the rim) of distinct vertices; device time of begin + finish (CUDA events)",
+                   "regenerate_ms": ms_max / args.steps}
+        for k in (1000, 100_000):
+            times, ents = [], 0
+            for rep in range(args.update_steps + 1):
+                rs, ps = r[sel.to(dev)].cpu().numpy(), phi[sel.to(dev)].cpu().numpy()
+                # no jumps to uniform radii: at n = 1e8 each such vertex would see ~5e6 others
+                ids, rn, pn = W.moves(rs, ps, R, k, 1000 * k + rep, jumps=0.0)
+                ids = sel.numpy()[ids].astype(np.int32)
+                ti, tr, tp = torch.tensor(ids), torch.tensor(rn), torch.tensor(pn)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                u = H.update_points(ctx, r, phi, off, col, R, ti, tr, tp, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if rep > 0:
+                    times.append(a.elapsed_time(b))
+                ents = u["stats"]["n_entries"]
+                off, col = u["row_off"], u["col_idx"]
+                del u
+            t = statistics.median(times)
+            dynamic["k%d" % k] = {"ms": t, "entries": ents, "vs_regenerate": t / dynamic["regenerate_ms"]}
+        del r, phi, off, col
 
     # the batched workload: 4096 small graphs per call, with the band width and
     # hub threshold of each size class picked by the tuner (untimed), and with
@@ -546,12 +588,27 @@ def main():
                            "path": "fp32 filter + fp64 recheck", "entries_per_step": n_entries,
                            "undirected_edges_per_s": value / 2,
                            "l2": "no flush: every step writes and reads >8 GB, far above the 126 MB L2"},
-                "fp64_plain": fp64, "batched": batched, "serving": serving, "properties": props, "stage_ms": stage, "e2e": e2e, "roofline": roof, "clocks": clocks,
-                "cpu_baseline": cpu, "paper_quadtree": quadtree, "gpu_launches": last.get("launches", 0) * args.steps,
-                "ties": last["ties"],
+                "e2e": e2e, "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
+                "gpu_launches": last.get("launches", 0) * args.steps, "ties": last["ties"],
+                "fp64_plain": fp64, "batched": batched, "serving": serving, "dynamic": dynamic, "stage_ms": stage,
+                "paper_quadtree": quadtree,
                 "job": {k: last[k] for k in ("R", "candidates", "rechecks", "ties", "bands", "hub_bands", "buckets",
                                              "hub_queries", "mid_rows", "big_rows", "mu", "rows_no_room",
-                                             "hub_rows_retraversed", "heavy_retries")}}
+                                             "hub_rows_retraversed", "heavy_retries")},
+                "properties": props,
+                # last, so that the end of the line carries the other workloads' figures
+                "summary": {"ms_per_step": round(ms_max / args.steps, 2), "ties": last["ties"],
+                            "fp64_plain_ms": fp64 and round(fp64["ms_per_step"], 2),
+                            "fp32_vs_fp64": fp64 and round(fp64["ms_per_step"] / (ms_max / args.steps), 2),
+                            "e2e_ms_median": e2e and round(e2e["ms_per_step"], 1),
+                            "batched_graphs_per_s": batched and round(batched["graphs_per_s"]),
+                            "batched_ms": batched and round(batched["ms_per_batch"], 2),
+                            "serving_p50_ms": serving and round(serving["p50_ms"], 2),
+                            "serving_p99_ms": serving and round(serving["p99_ms"], 2),
+                            "serving_mean_batch": serving and round(serving["mean_batch"], 2),
+                            "update_k1000_ms": dynamic and round(dynamic["k1000"]["ms"], 2),
+                            "update_k100000_ms": dynamic and round(dynamic["k100000"]["ms"], 2),
+                            "rim_count_frac_of_hbm": round(roof["frac"], 4)}}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:

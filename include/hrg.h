@@ -129,6 +129,15 @@ double hrg_expected_degree(int64_t n, double alpha, double R);
 int hrg_create(hrg_ctx **out, int device);
 int hrg_destroy(hrg_ctx *ctx);
 
+/* Device bytes the context's workspace holds now (it grows as jobs need it
+ * and stays until hrg_release_workspace or hrg_destroy).  Host only.
+ * Errors: HRG_EINVAL (null argument). */
+int hrg_workspace_bytes(const hrg_ctx *ctx, int64_t *bytes);
+
+/* Frees the context's workspace; the next job allocates what it needs again.
+ * Errors: HRG_EINVAL, HRG_ESTATE (a job is open), HRG_ECUDA. */
+int hrg_release_workspace(hrg_ctx *ctx);
+
 /*
  * hrg_generate_begin -- sampling, band structure, degree count, row offsets
  * (Algorithm 1 except the edge insertion).
@@ -437,9 +446,13 @@ int hrg_diameter_bounds(hrg_ctx *ctx, int64_t n, const int64_t *row_off, const i
  * hrg_server_create starts `slots` worker threads (1..64), each with its own
  * context (whose workspace, band structures included, stays resident across
  * requests) and stream.  A free worker admits the queued requests in arrival
- * order while their estimated device bytes (outputs plus transient workspace)
- * fit in mem_budget_bytes (<= 0: 70 % of the device's free memory at create),
- * and generates them together as one batch (hrg_generate_batch_begin);
+ * order while the device bytes they add fit in mem_budget_bytes (<= 0: 70 %
+ * of the device's free memory at create): their outputs, and the growth of
+ * the worker's workspace beyond what it already holds (estimated; measured
+ * once the batch is done, and counted as long as the workspace stays).  A
+ * worker that finds the next request too large while idle frees its own
+ * workspace first.  It generates the admitted requests together as one
+ * batch (hrg_generate_batch_begin);
  * requests arriving meanwhile join the next batch.  Batches of different
  * workers run concurrently on the device.  Results do not depend on the
  * batching: each equals hrg_generate of the same parameters.
@@ -470,9 +483,13 @@ typedef struct hrg_server_counters {
     int64_t batched_requests;  /* requests over all batches                   */
     int64_t queued;            /* requests waiting for admission               */
     int64_t max_running;       /* most batches in flight at once              */
-    int64_t in_use_bytes;      /* estimated device bytes admitted, unreleased  */
+    int64_t in_use_bytes;      /* device bytes counted against the budget: the
+                                  workers' resident workspaces (measured), the
+                                  outputs of unreleased requests and the
+                                  estimated workspace growth of running batches */
     int64_t peak_in_use_bytes; /* maximum of in_use_bytes                     */
     int64_t budget_bytes;
+    int64_t resident_bytes;    /* the workers' workspaces, measured after each batch */
 } hrg_server_counters;
 
 int hrg_server_create(hrg_server **out, int device, int32_t slots, int64_t mem_budget_bytes);

@@ -24,6 +24,7 @@ EXPORTS = (
     "hrg_generate_batch_begin", "hrg_server_create", "hrg_server_submit", "hrg_server_wait", "hrg_server_release",
     "hrg_server_stats", "hrg_server_last_error", "hrg_server_destroy", "hrg_graph_props", "hrg_degree_histogram",
     "hrg_add_random_edges", "hrg_bfs", "hrg_diameter_bounds", "hrg_set_limits", "hrg_update_begin",
+    "hrg_workspace_bytes", "hrg_release_workspace",
 )
 HRG_PROPS_TRIANGLES = 0x1
 
@@ -130,6 +131,8 @@ def load(build_if_missing: bool = True):
         L.hrg_diameter_bounds.argtypes = [_P, _I64, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32), _PI64, _PI64]
         L.hrg_set_limits.argtypes = [_P, ctypes.POINTER(hrg_limits)]
+        L.hrg_workspace_bytes.argtypes = [_P, _PI64]
+        L.hrg_release_workspace.argtypes = [_P]
         L.hrg_update_begin.argtypes = [_P, _I64, ctypes.c_double, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_uint32,
                                        ctypes.c_int32, _P, _P, ctypes.POINTER(_P), _PI64]
         L.hrg_add_random_edges.argtypes = [_P, _I64, _P, _P, _I64, ctypes.c_uint64, _P, _P, _P, _I64, _PI64, _PI64]
@@ -148,7 +151,8 @@ class hrg_result(ctypes.Structure):
 
 class hrg_server_counters(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("completed", "batches", "batched_requests", "queued", "max_running",
-                                               "in_use_bytes", "peak_in_use_bytes", "budget_bytes")]
+                                               "in_use_bytes", "peak_in_use_bytes", "budget_bytes",
+                                               "resident_bytes")]
 
 
 def hrg_solve_radius(n: int, alpha: float, avg_degree: float) -> float:
@@ -196,6 +200,16 @@ class Context:
     def check(self, rc):
         if rc != HRG_OK:
             raise HrgError(rc, self.last_error())
+
+    def workspace_bytes(self) -> int:
+        """hrg_workspace_bytes: device bytes of the context's workspace."""
+        v = ctypes.c_int64()
+        self.check(load().hrg_workspace_bytes(self.h, ctypes.byref(v)))
+        return v.value
+
+    def release_workspace(self):
+        """hrg_release_workspace: free the context's workspace."""
+        self.check(load().hrg_release_workspace(self.h))
 
     def set_limits(self, row_buffer_ids=0, hub_pool_ids=0, hub_runs=0, heavy_segments=0):
         """hrg_set_limits: capacities of the count pass's buffers for later

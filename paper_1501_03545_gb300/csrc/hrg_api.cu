@@ -237,6 +237,28 @@ extern "C" int hrg_destroy(hrg_ctx *ctx)
     return HRG_OK;
 }
 
+extern "C" int hrg_workspace_bytes(const hrg_ctx *ctx, int64_t *bytes)
+{
+    if (!ctx || !bytes) return HRG_EINVAL;
+    int64_t t = 0;
+    for (const auto &b : ctx->ws) t += (int64_t)b.bytes;
+    *bytes = t;
+    return HRG_OK;
+}
+
+extern "C" int hrg_release_workspace(hrg_ctx *ctx)
+{
+    if (!ctx) return HRG_EINVAL;
+    if (ctx->job.open) return set_err(ctx, HRG_ESTATE, "a job of this context is still open");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
+    for (auto &b : ctx->ws) {
+        if (b.ptr) cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    return HRG_OK;
+}
+
 extern "C" int hrg_set_limits(hrg_ctx *ctx, const hrg_limits *lim)
 {
     if (!ctx) return HRG_EINVAL;

@@ -70,7 +70,10 @@ struct hrg_server {
     std::deque<Req *> queue;
     std::unordered_map<int64_t, std::unique_ptr<Req>> reqs;
     int64_t next_ticket = 1;
+    // in_use = outputs of unreleased requests + the workers' resident
+    // workspaces (measured) + the estimated workspace growth of running batches
     size_t in_use = 0, peak_in_use = 0;
+    std::vector<size_t> resident;  // per worker: its context's workspace after its last batch
     bool stop = false;
     std::vector<std::thread> workers;
     std::string err;
@@ -95,15 +98,16 @@ int fail(hrg_server *s, int code, const char *fmt, ...)
 }
 
 // Device bytes of a request: outputs (r, phi, row offsets, neighbour ids at
-// 1.1 kbar per vertex) and the transient workspace of its generation (about
-// 250 bytes per vertex: ~80 of band structure and per-vertex lists, 128 of
-// kept-row buffer, 32 of hub-entry pool; plus the big-row sort buffer at up
-// to 4 bytes per entry and the pool's fixed 64 MB).
+// 1.1 kbar per vertex) and the workspace of its generation (about 260 bytes
+// per vertex: ~100 of band structure and per-vertex lists, 128 of kept-row
+// buffer, 32 of hub-entry pool; plus the big-row sort buffer at up to 4
+// bytes per entry and the pool's fixed 64 MB), with the 1/8 slack the
+// workspace grows by: 300 bytes per vertex.
 void estimate(const hrg_params &p, size_t &out, size_t &work)
 {
     const double n = (double)p.n, e = 1.1 * p.avg_degree * n + 1024.0;
     out = (size_t)(16.0 * n + 8.0 * (n + 1) + 4.0 * e) + 4096;
-    work = (size_t)(250.0 * n + 4.0 * e) + ((size_t)1 << 26);
+    work = (size_t)(300.0 * n + 4.5 * e) + ((size_t)1 << 26);
 }
 
 void run_batch(hrg_server *s, hrg_ctx *ctx, cudaStream_t st, std::vector<Req *> &batch)
@@ -188,7 +192,6 @@ void run_batch(hrg_server *s, hrg_ctx *ctx, cudaStream_t st, std::vector<Req *> 
         q->t_done = t;
         q->done = true;
         q->batch_size = count;
-        s->in_use -= q->est_work;
         if (rc == HRG_OK) {
             q->block = blk;
             q->first_pt = pts[k];
@@ -211,29 +214,53 @@ void worker_main(hrg_server *s, int slot)
     cudaStream_t st = nullptr;
     const bool ok = hrg_create(&ctx, s->device) == HRG_OK &&
                     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
-    (void)slot;
+    // the workspace beyond what this worker's context already holds
+    const auto growth = [&](size_t work) { return work > s->resident[slot] ? work - s->resident[slot] : (size_t)0; };
+    const auto fits = [&](const Req *q) { return s->in_use + q->est_out + growth(q->est_work) <= s->budget; };
     for (;;) {
         std::vector<Req *> batch;
+        size_t grown = 0;  // estimated workspace growth admitted with the batch
         {
             std::unique_lock<std::mutex> g(s->mu);
-            s->cv_work.wait(g, [&] {
-                return s->stop || (!s->queue.empty() &&
-                                   s->in_use + s->queue.front()->est_out + s->queue.front()->est_work <= s->budget);
-            });
+            for (;;) {
+                s->cv_work.wait(g, [&] {
+                    return s->stop || (!s->queue.empty() && (fits(s->queue.front()) || s->resident[slot] > 0));
+                });
+                if (s->stop || fits(s->queue.front())) break;
+                // too large while this worker idles on a resident workspace: free it
+                // (the other idle workers do the same when woken)
+                const size_t held = s->resident[slot];
+                g.unlock();
+                const bool freed = ok && hrg_release_workspace(ctx) == HRG_OK;
+                g.lock();
+                if (freed) {
+                    s->in_use -= held;
+                    s->resident[slot] = 0;
+                }
+                s->cv_work.notify_all();
+                if (!freed) {  // cannot shrink: wait for releases
+                    s->cv_work.wait(g, [&] { return s->stop || s->queue.empty() || fits(s->queue.front()); });
+                    if (s->stop) break;
+                }
+            }
             if (s->stop) break;  // the queue was cancelled
-            // admit in arrival order while the memory estimate fits
+            // admit in arrival order while the memory fits
             int64_t N = 0;
+            size_t work = 0, out = 0;
             while (!s->queue.empty() && (int32_t)batch.size() < s->max_batch) {
                 Req *q = s->queue.front();
-                const size_t need = q->est_out + q->est_work;
-                if (!batch.empty() && (s->in_use + need > s->budget || N + q->p.n > 0x7fffffffLL)) break;
-                if (batch.empty() && s->in_use + need > s->budget) break;
+                const size_t g2 = growth(work + q->est_work);
+                if (s->in_use + out + q->est_out + g2 > s->budget || (!batch.empty() && N + q->p.n > 0x7fffffffLL))
+                    break;
                 s->queue.pop_front();
-                s->in_use += need;
+                work += q->est_work;
+                out += q->est_out;
                 N += q->p.n;
                 q->t_start = now_s(s->t0);
                 batch.push_back(q);
             }
+            grown = growth(work);
+            s->in_use += out + grown;
             if (s->in_use > s->peak_in_use) s->peak_in_use = s->in_use;
             if (!batch.empty()) {
                 ++s->running;
@@ -249,14 +276,23 @@ void worker_main(hrg_server *s, int slot)
                 q->err = "worker could not create its context or stream";
                 q->done = true;
                 q->t_done = now_s(s->t0);
-                s->in_use -= q->est_out + q->est_work;
+                s->in_use -= q->est_out;
                 ++s->completed;
             }
+            s->in_use -= grown;
             --s->running;
             s->cv_done.notify_all();
             continue;
         }
         run_batch(s, ctx, st, batch);
+        // the estimate of the growth gives way to the workspace measured now
+        int64_t held = 0;
+        hrg_workspace_bytes(ctx, &held);
+        std::lock_guard<std::mutex> g(s->mu);
+        s->in_use = s->in_use - grown - s->resident[slot] + (size_t)held;
+        s->resident[slot] = (size_t)held;
+        if (s->in_use > s->peak_in_use) s->peak_in_use = s->in_use;
+        s->cv_work.notify_all();
     }
     if (st) {
         cudaStreamSynchronize(st);
@@ -277,6 +313,7 @@ extern "C" int hrg_server_create(hrg_server **out, int device, int32_t slots, in
     auto *s = new hrg_server();
     s->device = device;
     s->budget = mem_budget_bytes > 0 ? (size_t)mem_budget_bytes : (size_t)(0.7 * (double)free_b);
+    s->resident.assign(slots, 0);
     for (int k = 0; k < slots; ++k) s->workers.emplace_back(worker_main, s, k);
     *out = s;
     return HRG_OK;
@@ -379,6 +416,9 @@ extern "C" int hrg_server_stats(hrg_server *s, hrg_server_counters *out)
     out->in_use_bytes = (int64_t)s->in_use;
     out->peak_in_use_bytes = (int64_t)s->peak_in_use;
     out->budget_bytes = (int64_t)s->budget;
+    size_t res = 0;
+    for (size_t r : s->resident) res += r;
+    out->resident_bytes = (int64_t)res;
     return HRG_OK;
 }
 

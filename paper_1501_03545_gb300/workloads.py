@@ -120,14 +120,15 @@ def serving_requests(count: int, rate: float = SERVE_RATE, draw_seed: int = SERV
 # Vertex movement: the paper leaves the law of motion open, so the moves of a
 # dynamic update are synthetic inputs.
 # ---------------------------------------------------------------------------
-def moves(r, phi, R: float, k: int, seed: int):
+def moves(r, phi, R: float, k: int, seed: int, jumps: float = 0.15):
     """k distinct vertices and their new coordinates, from the current points
-    (numpy arrays r, phi) and numpy's generator seeded with ``seed``: 60 %
-    small steps (r + N(0, 0.3), phi + N(0, 1e-3)), 10 % to just beside
-    phi = 0 on either side (through the wrap point), 15 % to a radius
-    uniform on [0, R) (across bands, some to the centre), 15 % to the rim
-    (R - Exp(1)).  Returns (ids int32, r_new, phi_new) with 0 <= r_new < R
-    and 0 <= phi_new < 2 pi."""
+    (numpy arrays r, phi) and numpy's generator seeded with ``seed``: 10 % to
+    just beside phi = 0 on either side (through the wrap point), a fraction
+    ``jumps`` (default 15 %) to a radius uniform on [0, R) (across bands,
+    some to the centre, where a vertex sees most of the graph), 15 % to the
+    rim (R - Exp(1)), the rest small steps (r + N(0, 0.3), phi + N(0,
+    1e-3)).  Returns (ids int32, r_new, phi_new) with 0 <= r_new < R and
+    0 <= phi_new < 2 pi."""
     g = np.random.default_rng(seed)
     n = len(r)
     ids = np.sort(g.choice(n, size=k, replace=False)).astype(np.int32)
@@ -137,7 +138,7 @@ def moves(r, phi, R: float, k: int, seed: int):
     pn = p0 + g.normal(0.0, 1e-3, size=k)
     wrap = (kind >= 0.60) & (kind < 0.70)
     pn = np.where(wrap, g.normal(0.0, 1e-4, size=k), pn)
-    jump = (kind >= 0.70) & (kind < 0.85)
+    jump = (kind >= 0.70) & (kind < 0.70 + jumps)
     rn = np.where(jump, g.uniform(0.0, R, size=k), rn)
     rim = kind >= 0.85
     rn = np.where(rim, R - g.exponential(1.0, size=k), rn)

@@ -82,7 +82,9 @@ def test_large_workload_full_csr_against_oracle_and_fp64_path():
     _log("device: two generations, FP32 = FP64 compare and copies in %.1f s; %d entries, %d candidates, "
          "%d rechecks, ties %d (FP32 filter) / %d (FP64 path)" % (
              time.perf_counter() - t0, st["n_entries"], st["candidates"], st["rechecks"], st["ties"], st64["ties"]))
-    assert st["candidates"] == st64["candidates"]
+    # (candidate counts may differ between runs: the order inside an angular
+    # bucket comes from atomics, so the warps' shared hub windows can differ;
+    # the graph cannot)
     assert st["rows_no_room"] == 0 and st["hub_rows_retraversed"] == 0 and st["heavy_retries"] == 0
 
     R = st["R"]
