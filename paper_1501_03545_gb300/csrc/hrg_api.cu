@@ -112,7 +112,7 @@ struct hrg_job {
     const int32_t *move_ids = nullptr;
     uint32_t *moved = nullptr;
     int32_t *rem = nullptr, *gain = nullptr, *gain_cur = nullptr, *keep = nullptr;
-    int32_t compact_rows = 0;
+    int64_t old_entries = 0;
 };
 
 struct hrg_ctx {
@@ -125,7 +125,7 @@ struct hrg_ctx {
            W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_POSOF, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
            W_PACC, W_POUTDEG, W_POUTOFF, W_POUTCOL, W_PTRI, W_PSCAN, W_LRCNT, W_LROFF, W_LRLIST, W_LRFIN,
            W_LRDEG, W_HPOOL, W_HRUNS, W_HPCUR, W_BFSF0, W_BFSF1, W_BFSDEG, W_BFSOFF, W_BFSACC, W_BFSDIST,
-           W_MVBITS, W_MVREM, W_MVADD, W_MVCUR, W_MVKEEP, W_MVERR, W_COUNT };
+           W_MVBITS, W_MVREM, W_MVADD, W_MVCUR, W_MVKEEP, W_MVERR, W_MVSTART, W_MVWS, W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
     cudaEvent_t ev[10] = {};  // stage boundaries of the current job
@@ -913,14 +913,13 @@ extern "C" int hrg_update_begin(hrg_ctx *ctx, int64_t n, double R, double *r, do
 
     // 3. counts: the moved rows, the gains and the removals of the others
     QueryBufs &b = J.qb;
-    void *deg, *stats, *lists[3], *listcnt, *bigtot, *scanws, *compact;
+    void *deg, *stats, *lists[3], *listcnt, *bigtot, *scanws;
     if ((rc = ensure(ctx, hrg_ctx::W_DEG, sizeof(int32_t) * n, &deg))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_STATS, sizeof(uint64_t) * 8, &stats))) return rc;
     for (int c = 0; c < 3; ++c)
         if ((rc = ensure(ctx, hrg_ctx::W_LIST0 + c, sizeof(int32_t) * n, &lists[c]))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_LISTCNT, sizeof(int32_t) * 16, &listcnt))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_BIGTOT, sizeof(int64_t), &bigtot))) return rc;
-    if ((rc = ensure(ctx, hrg_ctx::W_RELIST0, sizeof(int32_t) * n, &compact))) return rc;
     if ((rc = ensure(ctx, hrg_ctx::W_SCAN, scan_workspace_bytes(n), &scanws))) return rc;
     b.r = r;
     b.phi = phi;
@@ -929,7 +928,6 @@ extern "C" int hrg_update_begin(hrg_ctx *ctx, int64_t n, double R, double *r, do
     for (int c = 0; c < 3; ++c) b.rows[c] = (int32_t *)lists[c];
     b.list_cnt = (int32_t *)listcnt;
     b.big_total = (int64_t *)bigtot;
-    b.relist[0] = (int32_t *)compact;
     CK(cudaMemsetAsync(stats, 0, sizeof(uint64_t) * 8, st));
     CK(cudaMemsetAsync(listcnt, 0, sizeof(int32_t) * 16, st));
     CK(cudaMemsetAsync(bigtot, 0, sizeof(int64_t), st));
@@ -940,9 +938,11 @@ extern "C" int hrg_update_begin(hrg_ctx *ctx, int64_t n, double R, double *r, do
                          nullptr, nullptr, st));
     CK(cudaEventRecord(ctx->ev[3], st));
     CK(launch_move_removed(k, ids, row_off, col_idx, (uint32_t *)moved, (int32_t *)rem, st));
-    MoveLists ml{{(int32_t *)lists[0], (int32_t *)lists[1], (int32_t *)lists[2], (int32_t *)compact}};
-    CK(launch_move_degrees(n, row_off, (uint32_t *)moved, (int32_t *)rem, (int32_t *)gain, (int32_t *)deg,
-                           (int32_t *)keep, ml, (int32_t *)listcnt, (unsigned long long *)bigtot, st));
+    MoveLists ml{{(int32_t *)lists[0], (int32_t *)lists[1], (int32_t *)lists[2]}};
+    void *rows_ws;
+    if ((rc = ensure(ctx, hrg_ctx::W_MVWS, move_rows_ws_bytes(on - o0), &rows_ws))) return rc;
+    CK(launch_move_degrees(n, on - o0, row_off, (uint32_t *)moved, (int32_t *)rem, (int32_t *)gain, (int32_t *)deg,
+                           (int32_t *)keep, ml, (int32_t *)listcnt, (unsigned long long *)bigtot, rows_ws, st));
     CK(cudaEventRecord(ctx->ev[4], st));
     // 4. row offsets
     CK(scan_i32_to_i64((int32_t *)deg, row_off_out, n, scanws, st));
@@ -954,8 +954,8 @@ extern "C" int hrg_update_begin(hrg_ctx *ctx, int64_t n, double R, double *r, do
     CK(cudaStreamSynchronize(st));
     memcpy(&J.n_entries, hp + 0, 8);
     memcpy(J.lists, hp + 8, 12);
-    memcpy(&J.compact_rows, hp + 20, 4);
     memcpy(&J.big_total, hp + 24, 8);
+    J.old_entries = on - o0;
     memcpy(J.stats, hp + 64, 64);
     J.open = true;
     *n_entries = J.n_entries;
@@ -974,8 +974,14 @@ static int update_finish(hrg_job *job, int32_t *col_out)
     CK(launch_move_query(p, job->qb, job->fp64, true, job->moves, job->move_ids, job->moved, nullptr, job->gain_cur,
                          job->keep, job->row_off, col_out, st));
     CK(cudaEventRecord(ctx->ev[7], st));
-    CK(launch_move_rows(n, job->old_off, job->old_col, job->moved, job->rem, job->qb.relist[0],
-                        job->qb.list_cnt + 3, job->compact_rows, job->row_off, col_out, st));
+    {
+        void *start_drop, *ws;
+        int rc;
+        if ((rc = ensure(ctx, hrg_ctx::W_MVSTART, sizeof(int32_t) * n, &start_drop))) return rc;
+        if ((rc = ensure(ctx, hrg_ctx::W_MVWS, move_rows_ws_bytes(job->old_entries), &ws))) return rc;  // held since begin
+        CK(launch_move_rows(n, job->old_entries, job->old_off, job->old_col, job->moved, job->rem,
+                            (int32_t *)start_drop, ws, job->row_off, col_out, st));
+    }
     CK(cudaEventRecord(ctx->ev[8], st));
     if (job->lists[0] > 0 || job->lists[1] > 0 || job->lists[2] > 0) {
         void *tmp = nullptr, *bws = nullptr;
@@ -1069,13 +1075,15 @@ extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
     if (job->update) {
         // check, apply, band counts, bucket histogram, bucket scan, scatter
         // (records + split, 2; the FP64 path 1), moved count, removals,
-        // degrees, row-offset scan; write: moved rows, flat copy (+ compaction),
-        // row sorts, gain check
+        // degrees, row-offset scan; write: moved rows, dropped-entry count,
+        // its scan and the copy, row sorts, gain check
         const int scatter = job->fp64 ? 1 : 2;
         int L = (job->moves > 0 ? 2 : 0) + 2 + scan_launches(job->plan.G) + scatter + (job->moves > 0 ? 2 : 0) + 1 +
                 scan_launches(job->plan.n);
+        const int64_t chunks = (job->old_entries + 4095) / 4096;
         if (job->finished)
-            L += (job->moves > 0 ? 1 : 0) + 1 + (job->compact_rows > 0 ? 1 : 0) + sort_launches(job->lists) + 1;
+            L += (job->moves > 0 ? 1 : 0) + (job->old_entries > 0 ? 4 + scan_launches(chunks) : 0) +
+                 sort_launches(job->lists) + 1;
         out->launches = L;
         out->hub_rows_retraversed = 0;
         out->hub_queries = 0;

@@ -202,16 +202,22 @@ cudaError_t launch_move_apply(int64_t k, const int32_t *ids, const double *r_new
 cudaError_t launch_move_removed(int64_t k, const int32_t *ids, const int64_t *row_off, const int32_t *col_idx,
                                 const uint32_t *moved, int32_t *rem, cudaStream_t s);
 // new degrees (deg: moved rows' counts in, all new degrees out), keep[w] =
-// old degree - removed; l[3]: rows to compact, l[0..2]: rows to sort by
-// length class as for the row sort (counts cnt[0..3] zeroed by the caller)
-struct MoveLists { int32_t *l[4]; };
-cudaError_t launch_move_degrees(int64_t n, const int64_t *row_off, const uint32_t *moved, const int32_t *rem,
-                                const int32_t *add, int32_t *deg, int32_t *keep, MoveLists lists, int32_t *cnt,
-                                unsigned long long *big_total, cudaStream_t s);
-// the rows of vertices that stay: untouched ones copied flat, the ones that lost entries compacted
-cudaError_t launch_move_rows(int64_t n, const int64_t *row_off, const int32_t *col_idx, const uint32_t *moved,
-                             const int32_t *rem, const int32_t *compact_rows, const int32_t *n_compact,
-                             int32_t compact_count, const int64_t *row_off_out, int32_t *col_out, cudaStream_t s);
+// old degree - removed; l[0..2]: rows to sort by length class as for the
+// row sort (counts cnt[0..2] zeroed by the caller)
+struct MoveLists { int32_t *l[3]; };
+// (ws: move_rows_ws_bytes(entries), kept until launch_move_rows; entries =
+// old entries from row_off[0]: the chunks of the flat copy that hold a changed
+// row are marked there)
+cudaError_t launch_move_degrees(int64_t n, int64_t entries, const int64_t *row_off, const uint32_t *moved,
+                                const int32_t *rem, const int32_t *add, int32_t *deg, int32_t *keep, MoveLists lists,
+                                int32_t *cnt, unsigned long long *big_total, void *ws, cudaStream_t s);
+// the rows of the vertices that stay, copied as one flat array of the old
+// entries (entries old entries from row_off[0]) without the moved vertices;
+// start_drop: int32[n] scratch, ws: move_rows_ws_bytes(entries)
+size_t move_rows_ws_bytes(int64_t entries);
+cudaError_t launch_move_rows(int64_t n, int64_t entries, const int64_t *row_off, const int32_t *col_idx,
+                             const uint32_t *moved, const int32_t *rem, int32_t *start_drop, void *ws,
+                             const int64_t *row_off_out, int32_t *col_out, cudaStream_t s);
 cudaError_t launch_move_check_gains(int64_t n, const int32_t *cnt, const int32_t *cur, unsigned long long *err,
                                     cudaStream_t s);
 
