@@ -314,11 +314,18 @@ static void plan_bands(Plan &p, int64_t n, double R, double alpha, int bands)
     const double tie_lo = p.rhs64 - 1e-12 * p.rhs64, tie_hi = p.rhs64 + 1e-12 * p.rhs64;
     memcpy(&p.tie_lo, &tie_lo, 8);
     memcpy(&p.tie_hi, &tie_hi, 8);
-    // Undecided band of the FP32 filter: the FP32 value carries a relative
-    // error below ~2^-19 from its inputs and operations, plus the difference
-    // between the fixed-point angle and the FP64 angles (<= ~2e-15 rad
-    // absolute), which near the threshold (|dphi| >= ~2 e^{-R/2}) is a relative
-    // error of at most ~1e-15 e^{R/2} on sin(dphi/2).
+    // Undecided band of the FP32 filter, relative to 1 + e^{-2R}.  The FP32
+    // value P_a M_b + P_b M_a + S_a S_b s^2 has non-negative terms, each
+    // within ~30 u (u = 2^-24) of its exact value: P, M within 3 u, S within
+    // 5 u, s = sin(dphi/2) within ~7 u (dA pi / 2^64 within 3 ulp, the sine's
+    // series and its evaluation), a few roundings; so the sum is within
+    // ~2e-6 relative.  The fixed-point angle difference dA is within 2^13
+    // units (2.8e-15 rad) of the FP64 angles' difference; that moves the
+    // third term by S_a S_b |dphi| 1.4e-15, and with S_a S_b dphi^2 / 4 <= 1
+    // near the threshold and S <= e^{R/2}, by at most 2.8e-15 e^{R/2}.  mu
+    // takes 2e-4 (100 times the first) plus 8e-15 e^{R/2} (almost 3 times the
+    // second); pairs outside [1 - mu, 1 + mu] are then decided as the exact
+    // predicate decides them, those inside are decided again in FP64.
     p.mu = f32(2e-4 + 8e-15 * std::exp(0.5 * R));
 }
 

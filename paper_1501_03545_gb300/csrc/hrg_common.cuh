@@ -319,11 +319,33 @@ __device__ __forceinline__ bool edge_pms64(const Plan &p, const PMS64 &q, const 
 // ---------------------------------------------------------------------------
 // Angular window of a query in a band (replaces Proposition 1 + the range
 // query of Algorithm 1).  For r_c >= b the admissible |dphi| is at most
-// theta(r_q, b) with sin^2(theta/2) = (cosh R - cosh(r_q - b)) /
-// (2 sinh r_q sinh b) = (1 + e^{-2R} - P_q M_b - P_b M_q) / (S_q S_b).
-// Computed in FP32 and padded so that it never excludes a neighbour; returns
-// the half-width in fixed-point angle units, or ~0 (all ones) for the whole
-// circle.
+// theta(r_q, b) with sin^2(theta/2) = X = (cosh R - cosh(r_q - b)) /
+// (2 sinh r_q sinh b) = (1 + e^{-2R} - P_q M_b - P_b M_q) / (S_q S_b): the
+// bound over the band is at its inner radius b, since dX/dr_c has the sign of
+// cosh r_q - cosh R cosh r_c < 0.  Computed in FP32 and padded so that it
+// never excludes a neighbour; returns the half-width in fixed-point angle
+// units, or ~0 (all ones) for the whole circle.
+//
+// Why the pads suffice (u = 2^-24, the FP32 unit roundoff):
+//  * inputs: P_q, M_q carry <= 3 u relative (expf <= 2 ulp, its argument kept
+//    to 2^-40 as a float pair), S_q <= 5 u (expm1f <= 1 ulp, the rounding of
+//    r to float moves e^{-2r} by <= u relative to 1 - e^{-2r}); the band
+//    constants and 1 + e^{-2R} are rounded once (<= u);
+//  * sub = P_q M_b + P_b M_q (non-negative terms) is within ~6 u relative,
+//    num = (1 + e^{-2R}) - sub within u (1 + e^{-2R}) + 6 u sub + u |num|
+//    absolute: below 1e-6 (1 + sub), covered 20 times by the absolute pad
+//    2e-5 (1 + sub);
+//  * den = S_q S_b (~7 u), its reciprocal (u) and the product (u): ~1e-6
+//    relative, covered by the relative pad 2e-5 on num, so X >= the exact X;
+//  * theta = 2 sqrt(X / (1 - X)) >= 2 asin(sqrt X) (X <= 1/4) or 2 asinf(sqrt
+//    X) (asinf <= 2 ulp, sqrtf and 1 - X <= u each): the X pad carries over
+//    as >= 9e-6 relative, above those ~5 u; theta is padded by 2e-5 more;
+//  * the fixed-point conversion multiplies by 2^64 / 2pi rounded up and
+//    rounds up, and adds 2^16 units: the angles A of the two endpoints are
+//    within 2^12 units of their exact values each (angle_key), so their
+//    difference within 2^13, covered 8 times.
+// The plain FP64 path uses the same windows: they are a superset; every
+// candidate inside is decided by the predicate.
 // ---------------------------------------------------------------------------
 constexpr uint64_t kFullCircle = 0xFFFFFFFFFFFFFFFFull;
 
@@ -347,15 +369,17 @@ __device__ __forceinline__ uint64_t window_halfwidth(const Plan &p, const PMS &q
     const float inv = __frcp_rn(den);
     const float sub = fmaf(q.P, Mb, Pb * q.M);
     const float num = p.rhs32 - sub;
-    // X = num / den, padded by 2e-5 relative and by the rounding of the difference
+    // X = num / den, padded by 2e-5 relative (the division's and den's
+    // roundings, ~1e-6) and 2e-5 (1 + sub) absolute (the difference's, ~1e-6 (1 + sub))
     float X = fmaf(num, 1.0f + 2e-5f, 2e-5f * (1.0f + sub)) * inv;
     if (X >= 1.0f) return kFullCircle;
     if (!(X > 0.0f)) X = 0.0f;
     // theta = 2 asin(sqrt X); for X <= 1/4 the bound asin(y) <= y / sqrt(1 - y^2)
     // (asin y = atan(y / sqrt(1 - y^2))) avoids asinf at < 9% extra width
     float th = X <= 0.25f ? 2.0f * sqrtf(X * __frcp_rn(1.0f - X)) : 2.0f * asinf(sqrtf(X));
-    th = th * (1.0f + 2e-5f) + 1e-30f;
+    th = th * (1.0f + 2e-5f) + 1e-30f;  // the asinf / sqrtf roundings (~5 u) and the scaling below (u)
     if (th >= 3.1415f) return kFullCircle;
+    // 2^16 units: the two endpoints' fixed-point angles are each within 2^12 of exact
     return float_to_u64_ru(th * kAngleScaleUp) + (1ull << 16);
 }
 

@@ -273,47 +273,49 @@ __global__ void k_scan_reduce(const Tin *__restrict__ in, int64_t N, Tacc *__res
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-// Down-sweep of one tile: warp w of the block owns the tile's elements
-// [w 32 kScanItems, (w + 1) 32 kScanItems) in the order j 32 + lane, so
-// every load and store of the warp touches consecutive addresses; each j is
-// scanned across the warp's lanes and carried on to the next.
+// Down-sweep of one tile.  The tile moves through shared memory twice so
+// that every global load and store of a warp touches consecutive addresses
+// while each thread scans kScanItems consecutive elements: loaded in the
+// order j kScanThreads + t, read back as t kScanItems + j, the results
+// written in place and stored in the first order.  Slot p + p/32 keeps the
+// per-thread reads free of bank conflicts.
+__device__ __forceinline__ int scan_slot(int p) { return p + (p >> 5); }
+
 template <typename Tin, typename Tout, typename Tacc>
-__global__ void k_scan_down(const Tin *__restrict__ in, int64_t N, const Tacc *__restrict__ offs,
-                            Tout *__restrict__ out, bool write_total)
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin *__restrict__ in, int64_t N,
+                                                            const Tacc *__restrict__ offs, Tout *__restrict__ out,
+                                                            bool write_total)
 {
     __shared__ Tacc wt[32];
     __shared__ Tacc tot;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t wbase = (int64_t)blockIdx.x * kTile + (int64_t)w * (32 * kScanItems);
-    Tacc v[kScanItems];
+    __shared__ Tacc buf[kTile + kTile / 32];
+    const int64_t base = (int64_t)blockIdx.x * kTile;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        const int64_t i = wbase + j * 32 + lane;
-        v[j] = i < N ? (Tacc)in[i] : Tacc(0);
+        const int p = j * kScanThreads + threadIdx.x;
+        const int64_t i = base + p;
+        buf[scan_slot(p)] = i < N ? (Tacc)in[i] : Tacc(0);
     }
-    Tacc carry = 0;  // the warp's elements before item j
+    __syncthreads();
+    Tacc s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) s += buf[scan_slot(threadIdx.x * kScanItems + j)];
+    Tacc run = block_exclusive_scan<Tacc>(s, wt, &tot) + (offs ? offs[blockIdx.x] : Tacc(0));
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        const Tacc x = v[j];
-        Tacc inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const Tacc y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        v[j] = carry + inc - x;  // exclusive prefix inside the warp
-        carry += __shfl_sync(0xffffffffu, inc, 31);
+        const int k = scan_slot(threadIdx.x * kScanItems + j);
+        const Tacc x = buf[k];
+        buf[k] = run;
+        run += x;
     }
-    // the warps' totals scanned across the block (lane 0 carries its warp's)
-    Tacc woff = block_exclusive_scan<Tacc>(lane == 0 ? carry : Tacc(0), wt, &tot);
-    woff = __shfl_sync(0xffffffffu, woff, 0) + (offs ? offs[blockIdx.x] : Tacc(0));
+    __syncthreads();
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        const int64_t i = wbase + j * 32 + lane;
-        if (i < N) out[i] = (Tout)(woff + v[j]);
+        const int p = j * kScanThreads + threadIdx.x;
+        const int64_t i = base + p;
+        if (i < N) out[i] = (Tout)buf[scan_slot(p)];
     }
-    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
-        out[N] = (Tout)(tot + (offs ? offs[blockIdx.x] : Tacc(0)));
+    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[N] = (Tout)run;
 }
 
 template <typename Tin, typename Tout>
