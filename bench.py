@@ -211,12 +211,13 @@ def reduce_over_ranks(ms, entries, dist, device):
     return float(t.item()), float(e.item())
 
 
-def run_serving(H, device, seconds, slots):
-    """Replays the serving workload's Poisson arrivals for `seconds` against
-    an hrg_server; latency = done - submit (server clock)."""
+def run_serving(H, device, seconds, slots, rate=W.SERVE_RATE):
+    """Replays the serving workload's Poisson arrivals (``rate`` requests/s)
+    for `seconds` against an hrg_server; latency = done - submit (server
+    clock)."""
     import queue
 
-    reqs = [q for q in W.serving_requests(int(W.SERVE_RATE * seconds * 1.5) + 16) if q[0] <= seconds]
+    reqs = [q for q in W.serving_requests(int(rate * seconds * 1.5) + 16, rate=rate) if q[0] <= seconds]
     srv = H.Server(device, slots=slots)
     try:
         # warm-up: grow every worker's resident workspace to the largest request size
@@ -260,14 +261,14 @@ def run_serving(H, device, seconds, slots):
     span = max(d for (_, _, d, _, _) in done) - min(s for (_, s, _, _, _) in done)
     ents = sum(e for (_, _, _, e, _) in done)
     q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
-    return {"requests": len(done), "failed": sum(1 for x in done if x[0] != 0), "offered_rate_req_s": W.SERVE_RATE,
+    return {"requests": len(done), "failed": sum(1 for x in done if x[0] != 0), "offered_rate_req_s": rate,
             "arrival_seconds": seconds, "span_s": span, "p50_ms": q(0.50), "p99_ms": q(0.99),
             "mean_ms": statistics.mean(lat), "throughput_entries_s": ents / span,
             "throughput_req_s": len(done) / span, "entries": ents,
             "mean_batch": (c1["batched_requests"] - base["batched_requests"]) / max(1, c1["batches"] - base["batches"]),
             "max_running": c1["max_running"], "slots": slots,
             "recipe": "Poisson arrivals at %g req/s, n log-uniform [1e3, 3e7], alpha U[0.55, 1.5], kbar U[4, 32], "
-                      "seed 10000 + index, numpy draw seed %d" % (W.SERVE_RATE, W.SERVE_DRAW_SEED)}
+                      "seed 10000 + index, numpy draw seed %d" % (rate, W.SERVE_DRAW_SEED)}
 
 
 def run_properties(H, ctx, stream, graphs):
@@ -540,8 +541,12 @@ def main():
 
     # serving: Poisson arrivals of mixed requests, continuous batching
     serving = None
+    serving_x3 = None
     if args.serve_seconds > 0 and rank == 0:
         serving = run_serving(H, local, args.serve_seconds, args.serve_slots)
+        # the same mix at three times the rate (near the device's capacity):
+        # requests wait for each other, so batches form
+        serving_x3 = run_serving(H, local, min(3.0, args.serve_seconds), args.serve_slots, rate=3 * W.SERVE_RATE)
 
     # graph properties of Sec. 4.1 and the random long-range edges of Sec. 4.2
     # on the device: the 1e6-vertex workload (the size of the paper's property
@@ -590,7 +595,8 @@ def main():
                            "l2": "no flush: every step writes and reads >8 GB, far above the 126 MB L2"},
                 "e2e": e2e, "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
                 "gpu_launches": last.get("launches", 0) * args.steps, "ties": last["ties"],
-                "fp64_plain": fp64, "batched": batched, "serving": serving, "dynamic": dynamic, "stage_ms": stage,
+                "fp64_plain": fp64, "batched": batched, "serving": serving, "serving_x3": serving_x3,
+                "dynamic": dynamic, "stage_ms": stage,
                 "paper_quadtree": quadtree,
                 "job": {k: last[k] for k in ("R", "candidates", "rechecks", "ties", "bands", "hub_bands", "buckets",
                                              "hub_queries", "mid_rows", "big_rows", "mu", "rows_no_room",
@@ -606,6 +612,9 @@ def main():
                             "serving_p50_ms": serving and round(serving["p50_ms"], 2),
                             "serving_p99_ms": serving and round(serving["p99_ms"], 2),
                             "serving_mean_batch": serving and round(serving["mean_batch"], 2),
+                            "serving_x3_p50_ms": serving_x3 and round(serving_x3["p50_ms"], 2),
+                            "serving_x3_p99_ms": serving_x3 and round(serving_x3["p99_ms"], 2),
+                            "serving_x3_mean_batch": serving_x3 and round(serving_x3["mean_batch"], 2),
                             "update_k1000_ms": dynamic and round(dynamic["k1000"]["ms"], 2),
                             "update_k100000_ms": dynamic and round(dynamic["k100000"]["ms"], 2),
                             "rim_count_frac_of_hbm": round(roof["frac"], 4)}}

@@ -339,8 +339,12 @@ static void plan_buckets(Plan &p, const int64_t *cnt, int32_t *p_hub, double hub
     p.sbits = sb;
     int64_t G = 0;
     for (int k = 0; k < p.B; ++k) {
+        // about one point per bucket; twice as many buckets in bands of more
+        // than 2^16 points, where a rim window's bucket range then carries
+        // fewer points outside the window (the candidates the window test rejects)
         int g = 0;
         while (g < 40 && ((int64_t)1 << (g + 1)) <= cnt[k]) ++g;
+        if (cnt[k] > ((int64_t)1 << 16)) ++g;
         if (g < sb) g = sb;
         p.gbits[k] = g;
         p.base[k] = G;
