@@ -172,15 +172,24 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__res
 // sorted on its own: by one thread (insertion) up to 32 keys, by one warp
 // (bitonic) beyond, so skewed inputs stay correct.
 // --------------------------------------------------------------------------
-constexpr int kMaxSortBuckets = 8192;
-
-struct SortSmem {
-    uint32_t tmp[kSmemRow];
-    uint32_t cnt[kMaxSortBuckets + 1];
+// Shared memory of the CTA sort of up to CAP keys: m keys use the smallest
+// power of two above m/4 buckets, at most BK.  Rows take up to kSmemRow keys;
+// the big rows' id buckets expect 2048..4096 keys each and take up to
+// kItemCap (twice that: a larger bucket, which uniformly spread ids make
+// vanishingly rare, goes to the global-memory network), so their CTAs need
+// less shared memory and four fit on an SM.
+template <int CAP, int BK>
+struct SortSmemT {
+    uint32_t tmp[CAP];
+    uint32_t cnt[BK + 1];
     uint32_t wsum[kCtaWarps];
+    static constexpr uint32_t kBuckets = BK;
 };
+using SortSmem = SortSmemT<kSmemRow, 4096>;  // rows of up to kSmemRow keys use at most 4096 buckets
+constexpr int kItemCap = 8191;
+using ItemSmem = SortSmemT<kItemCap, 2048>;
 
-// in-place exclusive scan of c[0..nb) (nb <= kMaxSortBuckets) by the whole CTA
+// in-place exclusive scan of c[0..nb) (nb at most the sort's bucket count) by the whole CTA
 __device__ void cta_exclusive_scan(uint32_t *c, uint32_t nb, uint32_t *wsum)
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -206,11 +215,12 @@ __device__ void cta_exclusive_scan(uint32_t *c, uint32_t nb, uint32_t *wsum)
     __syncthreads();
 }
 
-__device__ void sort_span(SortSmem &S, const int32_t *src, int32_t *dst, int m, int32_t lo, uint32_t range)
+template <typename SM>
+__device__ void sort_span(SM &S, const int32_t *src, int32_t *dst, int m, int32_t lo, uint32_t range)
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     uint32_t nb = 1;
-    while (nb * 4 <= (uint32_t)m && nb < kMaxSortBuckets) nb <<= 1;
+    while (nb * 4 <= (uint32_t)m && nb < SM::kBuckets) nb <<= 1;
     if (range == 0) range = 1;
     const uint32_t mul = bucket_mul(nb, range);
     for (uint32_t i = t; i <= nb; i += kCtaThreads) S.cnt[i] = 0;
@@ -390,7 +400,7 @@ __global__ void k_big_scan(const BigRow *__restrict__ br, const int64_t *__restr
             if (v > 0) {
                 const int64_t lo = bucket_lo(i, mul), hi = min(R.range, bucket_lo(i + 1, mul));
                 Item it{R.tmp_off + st, rbase + st, v, (int32_t)lo, (uint32_t)(hi - lo), 0};
-                if (v <= kSmemRow) items[atomicAdd(n_items, 1)] = it;
+                if (v <= kItemCap) items[atomicAdd(n_items, 1)] = it;
                 else slow[atomicAdd(n_slow, 1)] = it;
             }
         }
@@ -444,7 +454,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_sort_items(const Item *__restri
                                                              int32_t *__restrict__ col_idx)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    SortSmem &S = *reinterpret_cast<SortSmem *>(smraw);
+    ItemSmem &S = *reinterpret_cast<ItemSmem *>(smraw);
     const int32_t nit = *n_items;
     for (int32_t k = blockIdx.x; k < nit; k += gridDim.x) {
         const Item it = items[k];
@@ -505,7 +515,7 @@ cudaError_t launch_sort_rows(const Plan &p, const QueryBufs &b, const int32_t co
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_sort_cta_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
-        cudaFuncSetAttribute(k_sort_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
+        cudaFuncSetAttribute(k_sort_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ItemSmem));
         attr = true;
     }
     if (counts[0] > 0)
@@ -536,7 +546,7 @@ cudaError_t launch_sort_rows(const Plan &p, const QueryBufs &b, const int32_t co
         k_big_scan<<<n_big, 1024, 0, s>>>(br, row_off, p.n, hist, items, ctr, slow, ctr + 1);
         k_big_scatter<<<gc, 256, 0, s>>>(br, n_big, row_off, p.n, col_idx, hist, tmp);
         const unsigned gi = (unsigned)std::min<int64_t>(nbk_sum, 152 * 8);
-        k_sort_items<<<gi, kCtaThreads, sizeof(SortSmem), s>>>(items, ctr, tmp, col_idx);
+        k_sort_items<<<gi, kCtaThreads, sizeof(ItemSmem), s>>>(items, ctr, tmp, col_idx);
         k_sort_slow<<<64, 1024, 0, s>>>(slow, ctr + 1, tmp, col_idx);
     }
     return cudaGetLastError();
