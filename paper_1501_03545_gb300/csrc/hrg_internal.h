@@ -87,19 +87,20 @@ __device__ __forceinline__ void warp_bitonic64(int32_t &a, int32_t &b, int lane)
     }
 }
 
-// Up to 128 ids sorted the same way with four registers a lane: element
-// i = lane + 32 r in v[r].  Partners 32 or 64 apart sit inside a lane
-// (registers r and r | j/32), nearer ones are exchanged by shuffles.
-__device__ __forceinline__ void warp_bitonic128(int32_t (&v)[4], int lane)
+// Up to 32 R ids sorted the same way with R registers a lane (R = 2, 4, 8):
+// element i = lane + 32 r in v[r].  Partners 32 or more apart sit inside a
+// lane (registers r and r | j/32), nearer ones are exchanged by shuffles.
+template <int R>
+__device__ __forceinline__ void warp_bitonic_regs(int32_t (&v)[R], int lane)
 {
 #pragma unroll
-    for (int k = 2; k <= 128; k <<= 1) {
+    for (int k = 2; k <= 32 * R; k <<= 1) {
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
             if (j >= 32) {
                 const int rj = j >> 5;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
+                for (int r = 0; r < R; ++r) {
                     if (r & rj) continue;  // r is the lower index of the pair (r, r | rj)
                     const bool up = ((lane + 32 * r) & k) == 0;
                     const int32_t lo = min(v[r], v[r | rj]), hi = max(v[r], v[r | rj]);
@@ -109,7 +110,7 @@ __device__ __forceinline__ void warp_bitonic128(int32_t (&v)[4], int lane)
             } else {
                 const bool lower = (lane & j) == 0;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
+                for (int r = 0; r < R; ++r) {
                     const int32_t p = __shfl_xor_sync(0xffffffffu, v[r], j);
                     const bool up = ((lane + 32 * r) & k) == 0;
                     v[r] = (lower == up) ? min(v[r], p) : max(v[r], p);
@@ -118,6 +119,8 @@ __device__ __forceinline__ void warp_bitonic128(int32_t (&v)[4], int lane)
         }
     }
 }
+
+__device__ __forceinline__ void warp_bitonic128(int32_t (&v)[4], int lane) { warp_bitonic_regs<4>(v, lane); }
 
 struct QueryBufs {
     const uint64_t *A;        // [n] fixed-point angles, bucket order

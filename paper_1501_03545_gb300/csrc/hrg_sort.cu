@@ -115,6 +115,18 @@ __device__ __forceinline__ void warp_sort64(int32_t *row, int d, int lane)
     if (lane + 32 < d) row[lane + 32] = b;
 }
 
+template <int R>
+__device__ __forceinline__ void warp_sort_regs(int32_t *row, int d, int lane)
+{
+    int32_t v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = lane + 32 * r < d ? row[lane + 32 * r] : 0x7fffffff;
+    warp_bitonic_regs<R>(v, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (lane + 32 * r < d) row[lane + 32 * r] = v[r];
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ cnt,
                                                             int64_t n, const int32_t *__restrict__ graph_of,
                                                             const int64_t *__restrict__ noff,
@@ -131,6 +143,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__res
     int32_t *row = col_idx + base;
     if (d <= 64) {  // uniform per warp
         warp_sort64(row, d, lane);
+        return;
+    }
+    if (d <= 256) {  // a bitonic network over the warp's registers: four or eight ids a lane
+        if (d <= 128) warp_sort_regs<4>(row, d, lane);
+        else warp_sort_regs<8>(row, d, lane);
         return;
     }
     uint32_t nb = 1;
