@@ -49,6 +49,15 @@ ORACLE_SAMPLE_N = 2_000_000
 NCU_TRAFFIC = {"06e85754858d1c0c": (281.825536e6 + 359.747840e6) / 4e6}
 
 
+# Warp instructions of one launch of the dominant kernel at the timed workload
+# (smsp__inst_executed.sum of one ncu capture at n = 1e8, a one-pass metric),
+# keyed like the traffic record.
+NCU_INSTRUCTIONS = {}
+
+# issue slots per second at the maximum SM clock: 152 SMs x 4 schedulers x 2.07 GHz
+ISSUE_PEAK = 152 * 4 * 2.07e9
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -578,6 +587,13 @@ def main():
                 "ms": stage["count"] + stage["offsets"] + stage["write"] + stage["rowsort"]}}
     qc = roof["query_csr_roofline"]
     qc["frac"] = qc["bytes"] / (qc["ms"] / 1e3) / 1e9 / peak
+    # the roof that binds this kernel: instruction issue (see DESIGN: 60 % of
+    # issue slots used, 8 % of DRAM throughput)
+    inst = NCU_INSTRUCTIONS.get(source_hash()) if w.n == WORKLOAD.n else None
+    roof["issue_roof"] = None if inst is None else {
+        "warp_instructions": inst, "achieved": inst / (stage["count_rim"] / 1e3), "peak": ISSUE_PEAK,
+        "unit": "warp instructions/s", "frac": inst / (stage["count_rim"] / 1e3) / ISSUE_PEAK,
+        "peak_kind": "152 SMs x 4 schedulers x 2.07 GHz (maximum SM clock)"}
 
     cpu = quadtree = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -241,12 +241,11 @@ __device__ __forceinline__ float lhs32(const PMS &q, const PMS &c, int64_t dA)
     const uint32_t lo = (uint32_t)ad;
     const float half = fmaf((float)hi, 7.3145904e-10f /* pi / 2^32 */, (float)lo * 1.7030608e-19f /* pi / 2^64 */);
     const float s = sin_taylor(half);
-    // operands in a fixed order (smaller id first) so that the decision on a
-    // pair is the same whichever endpoint asks
-    const bool sw = q.id > c.id;
-    const float aP = sw ? c.P : q.P, aM = sw ? c.M : q.M;
-    const float bP = sw ? q.P : c.P, bM = sw ? q.M : c.M;
-    return fmaf(q.S * c.S, s * s, fmaf(aP, bM, bP * aM));
+    // both products rounded on their own and then added: rounded addition and
+    // multiplication commute, so the value of a pair is the same whichever
+    // endpoint asks (no fused multiply-add across the two cross products)
+    const float cross = __fadd_rn(__fmul_rn(q.P, c.M), __fmul_rn(c.P, q.M));
+    return fmaf(__fmul_rn(q.S, c.S), s * s, cross);
 }
 
 // sin(x) for |x| <= 2^-4 by Taylor through x^9 (error < x^11/11! < 1e-20 |x|),
