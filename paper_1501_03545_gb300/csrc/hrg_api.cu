@@ -292,6 +292,7 @@ static void plan_bands(Plan &p, int64_t n, double R, double alpha, int bands)
     p.coshR = std::cosh(R);
     p.alpha = alpha;
     p.big = std::cosh(alpha * R) - 1.0;
+    p.big53 = std::ldexp(p.big, -53);
     p.inv_alpha = 1.0 / alpha;
     p.half_R = 0.5 * R;
     p.half_R_hi = (float)p.half_R;

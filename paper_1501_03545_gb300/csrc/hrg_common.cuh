@@ -22,6 +22,7 @@ struct Plan {
     int64_t n;
     double R, coshR, alpha;
     double big;          // cosh(alpha R) - 1, the scale of Eq. (1)'s inverse CDF
+    double big53;        // big 2^-53 (exact): multiplies the top 53 bits of a random word
     double inv_alpha;    // 1 / alpha
     double half_R;       // R / 2
     float half_R_hi, half_R_lo;  // R / 2 as a float pair (hi + lo)
@@ -122,25 +123,31 @@ __device__ __forceinline__ double acosh_series(double x, const double *log_tab)
     return a;
 }
 
-// Radius of Eq. (1)'s inverse CDF, r = acosh(x) / alpha with x = 1 + u_r
-// (cosh(alpha R) - 1).  Above x = 2^8 the series (no square root, and one
-// short branch where the library acosh would make a warp run both paths);
-// below, the library acosh.
-__device__ __forceinline__ double radius_of(double u_r, double big, double inv_alpha, const double *log_tab)
+// The uniform of a 64-bit word is u = k 2^-53, k its top 53 bits.  Its
+// products are taken as k (c 2^-53): c 2^-53 is c with the exponent moved
+// (exact), and k and u differ by a power of two too, so k (c 2^-53) and u c
+// are the same real number and round to the same double -- one multiply
+// instead of two.
+__device__ __forceinline__ double top53(uint32_t hi, uint32_t lo)
 {
-    const double x = __dadd_rn(1.0, __dmul_rn(u_r, big));
+    const uint64_t w = ((uint64_t)hi << 32) | (uint64_t)lo;
+    return (double)(w >> 11);  // exact: below 2^53
+}
+
+// Radius of Eq. (1)'s inverse CDF, r = acosh(x) / alpha with x = 1 + u_r
+// (cosh(alpha R) - 1) = 1 + k_r big_scaled, big_scaled = (cosh(alpha R) - 1)
+// 2^-53.  Above x = 2^8 the series (no square root, and one short branch
+// where the library acosh would make a warp run both paths); below, the
+// library acosh.
+__device__ __forceinline__ double radius_of(double k_r, double big_scaled, double inv_alpha, const double *log_tab)
+{
+    const double x = __dadd_rn(1.0, __dmul_rn(k_r, big_scaled));
     const double a = x >= 0x1p8 ? acosh_series(x, log_tab) : acosh(x);
     return a * inv_alpha;
 }
 
-// the uniform on [0,1) made of the top 53 bits of a 64-bit word
-__device__ __forceinline__ double unit53(uint32_t hi, uint32_t lo)
-{
-    const uint64_t w = ((uint64_t)hi << 32) | (uint64_t)lo;
-    return (double)(w >> 11) * 0x1.0p-53;
-}
-
 constexpr double kTwoPi = 6.283185307179586;          // the double nearest 2 pi
+constexpr double kTwoPiScaled = kTwoPi * 0x1.0p-53;    // (the double nearest 2 pi) 2^-53, exact
 constexpr double kAngleScale = 2.9358905032820014e18;  // 2^64 / (2 pi): angle -> 64-bit fixed point
 constexpr float kAngleScaleUp = 2.9358906e18f;         // the same, rounded up (windows stay conservative)
 constexpr float kAngleUnit = 3.4061215800865545e-19f;  // 2 pi / 2^64
@@ -154,6 +161,16 @@ __device__ __forceinline__ uint64_t angle_key(double phi)
     if (!(a > 0.0)) return 0ull;
     if (a >= 18446744073709551615.0) return 0xFFFFFFFFFFFFFFFFull;
     return __double2ull_rz(a);
+}
+
+// The sampler files a point under the bucket of u_phi 2^64 = its word's top
+// 53 bits shifted back (integer work only), not of angle_key(phi): phi =
+// fl(u_phi 2pi), so the two are within 2^12 units of each other, and a
+// window's 2^16-unit pad (window_halfwidth) covers that as well as the
+// stored angles' own 2^12 -- no bucket range misses a point in the window.
+__device__ __forceinline__ uint64_t sampled_angle_key(const U4 &w)
+{
+    return (((uint64_t)w.x << 32) | (uint64_t)w.y) & ~(uint64_t)0x7FF;
 }
 
 // radial band: the k with band_lo[k] <= r < band_lo[k+1]
@@ -342,7 +359,8 @@ __device__ __forceinline__ bool edge_pms64(const Plan &p, const PMS64 &q, const 
 //  * the fixed-point conversion multiplies by 2^64 / 2pi rounded up and
 //    rounds up, and adds 2^16 units: the angles A of the two endpoints are
 //    within 2^12 units of their exact values each (angle_key), so their
-//    difference within 2^13, covered 8 times.
+//    difference within 2^13, and a sampled point is filed by a key within
+//    2^12 of its A (sampled_angle_key): 3 2^12 in all, covered 5 times.
 // The plain FP64 path uses the same windows: they are a superset; every
 // candidate inside is decided by the predicate.
 // ---------------------------------------------------------------------------
@@ -378,7 +396,8 @@ __device__ __forceinline__ uint64_t window_halfwidth(const Plan &p, const PMS &q
     float th = X <= 0.25f ? 2.0f * sqrtf(X * __frcp_rn(1.0f - X)) : 2.0f * asinf(sqrtf(X));
     th = th * (1.0f + 2e-5f) + 1e-30f;  // the asinf / sqrtf roundings (~5 u) and the scaling below (u)
     if (th >= 3.1415f) return kFullCircle;
-    // 2^16 units: the two endpoints' fixed-point angles are each within 2^12 of exact
+    // 2^16 units: the two endpoints' fixed-point angles are each within 2^12
+    // of exact, and a sampled point's filing key within 2^12 of its angle
     return float_to_u64_ru(th * kAngleScaleUp) + (1ull << 16);
 }
 

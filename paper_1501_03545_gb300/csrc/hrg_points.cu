@@ -63,14 +63,14 @@ __global__ void k_sample_bucket(Plan p, uint64_t seed, double *__restrict__ r_ou
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
         const U4 w = philox_block((uint64_t)i, seed);
-        const double u_phi = unit53(w.x, w.y);
-        const double u_r = unit53(w.z, w.w);
-        const double ph = __dmul_rn(u_phi, kTwoPi);
-        const double rr = radius_of(u_r, p.big, p.inv_alpha, s_tab);
+        const double k_phi = top53(w.x, w.y);
+        const double k_r = top53(w.z, w.w);
+        const double ph = __dmul_rn(k_phi, kTwoPiScaled);  // = u_phi 2pi, rounded once
+        const double rr = radius_of(k_r, p.big53, p.inv_alpha, s_tab);
         phi_out[i] = ph;
         r_out[i] = rr;
         const int band = band_of(p, rr);
-        const int64_t g = bucket_of(p, band, angle_key(ph));
+        const int64_t g = bucket_of(p, band, sampled_angle_key(w));
         gbuf[i] = (int32_t)g;
         slot[i] = atomicAdd(&cnt[g], 1);
         atomicAdd(&sh[band], 1);
@@ -179,13 +179,13 @@ __global__ void k_sample_bucket_batch(const Plan *__restrict__ plans, const int3
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
         const Plan &p = plans[__ldg(graph_of + i)];
         const U4 w = philox_block((uint64_t)(i - p.id_off), p.seed);
-        const double u_phi = unit53(w.x, w.y);
-        const double u_r = unit53(w.z, w.w);
-        const double ph = __dmul_rn(u_phi, kTwoPi);
-        const double rr = radius_of(u_r, p.big, p.inv_alpha, s_tab);
+        const double k_phi = top53(w.x, w.y);
+        const double k_r = top53(w.z, w.w);
+        const double ph = __dmul_rn(k_phi, kTwoPiScaled);  // = u_phi 2pi, rounded once
+        const double rr = radius_of(k_r, p.big53, p.inv_alpha, s_tab);
         phi_out[i] = ph;
         r_out[i] = rr;
-        const int64_t g = bucket_of(p, band_of(p, rr), angle_key(ph));
+        const int64_t g = bucket_of(p, band_of(p, rr), sampled_angle_key(w));
         gbuf[i] = (int32_t)g;
         slot[i] = atomicAdd(&cnt[g], 1);
     }
