@@ -439,17 +439,25 @@ def main():
         # each step is one call (generation + read-back into pinned host
         # memory, which the host's other tenants share: the spread between
         # steps is reported, the median is the value)
-        per = []
+        per, d2h, chunks = [], [], 0
         for _ in range(args.e2e_steps):
             t0 = time.perf_counter()
-            ne, _ = H.generate_host(ctx, n, w.alpha, w.kbar, seed, rh, ph, oh, ch)
+            ne, hst = H.generate_host(ctx, n, w.alpha, w.kbar, seed, rh, ph, oh, ch)
             per.append(time.perf_counter() - t0)
+            d2h.append(hst["d2h_ms"])
+            chunks = hst["write_chunks"]
         es = statistics.median(per)
         srt = sorted(per)
+        nbytes = int(16 * n + 8 * (n + 1) + 4 * ne)
+        # the copies run from the sampler's end to the last range's read-back:
+        # d2h_ms is that span on the copy stream, its rate the link's (when
+        # the copies, not the generation, set the pace)
         e2e = {"value": ne / es, "unit": UNIT, "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": int(16 * n + 8 * (n + 1) + 4 * ne), "ms_per_step": 1e3 * es,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": 1e3 * es,
                "ms_min": 1e3 * srt[0], "ms_p90": 1e3 * srt[min(len(srt) - 1, int(0.9 * len(srt)))],
-               "ms_steps": [round(1e3 * x, 1) for x in per], "statistic": "median over steps"}
+               "ms_steps": [round(1e3 * x, 1) for x in per], "statistic": "median over steps",
+               "write_chunks": chunks, "d2h_ms_steps": [round(x, 1) for x in d2h],
+               "d2h_span_gbs_median": round(nbytes / (statistics.median(d2h) * 1e6), 1) if d2h else None}
         del rh, ph, oh, ch
 
     # plain FP64 path on the same graph

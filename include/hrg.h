@@ -97,6 +97,14 @@ typedef struct hrg_stats {
     int64_t rows_no_room;
     int32_t hub_rows_retraversed;
     int32_t heavy_retries;
+    /* id ranges the neighbour write ran in: 1, or (hrg_generate_host, graphs
+     * of 2^26 entries or more) up to 8, each range's ids going back to the
+     * host while the next is written and sorted; stage_ms[5..7] are then
+     * sums over the ranges */
+    int32_t write_chunks;
+    /* hrg_generate_host only (else -1): ms from the first device-to-host copy
+     * (the points, as soon as they are sampled) to the end of the last */
+    float d2h_ms;
 } hrg_stats;
 
 typedef struct hrg_ctx hrg_ctx;
@@ -290,9 +298,13 @@ int hrg_generate(hrg_ctx *ctx, const hrg_params *p, void *stream, double *r_out,
  * row_off and col_idx back (r_host double[n], phi_host double[n],
  * row_off_host int64[n+1], col_idx_host int32[col_capacity]).  Host buffers
  * registered with cudaHostRegister (or pinned) copy at full link speed.
- * The context generates on a stream of its own; r, phi and row_off travel
- * back on a second one while the neighbour ids are written and sorted.
- * The call returns when every copy is complete.
+ * The context generates on a stream of its own and copies on a second one:
+ * r and phi as soon as the sampler has written them, row_off once the
+ * degrees are counted, and, for graphs of 2^26 entries or more, the
+ * neighbour ids in up to 8 id ranges, each as soon as its rows are written
+ * and sorted while the next range is (stats_out->write_chunks, d2h_ms).
+ * The call returns when every copy is complete; the host buffers must not be
+ * read before.
  * Errors as hrg_generate.
  */
 int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_host, double *phi_host, int64_t *row_off_host,

@@ -48,7 +48,7 @@ class hrg_stats(ctypes.Structure):
                 ("big_rows", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mu", ctypes.c_float),
                 ("stage_ms", ctypes.c_float * 8), ("launches", ctypes.c_int32), ("ties", ctypes.c_uint64),
                 ("rows_no_room", ctypes.c_int64), ("hub_rows_retraversed", ctypes.c_int32),
-                ("heavy_retries", ctypes.c_int32)]
+                ("heavy_retries", ctypes.c_int32), ("write_chunks", ctypes.c_int32), ("d2h_ms", ctypes.c_float)]
 
     STAGES = ("sample", "bands", "count_hub", "count_rim", "offsets", "write_hub", "write_rim", "rowsort")
 

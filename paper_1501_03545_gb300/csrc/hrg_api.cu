@@ -89,6 +89,7 @@ struct hrg_job {
     bool hub_pooled = false;  // the count pass kept every hub entry: the write pass copies them
     int32_t hub_runs = 0;
     int32_t heavy_retries = 0;  // count passes repeated for lack of room in the list of long hub ranges
+    int32_t write_chunks = 1;   // id ranges of the write pass (hrg_generate_host)
     bool open = false;
     bool finished = false;
     int32_t p_hub = 0;
@@ -115,6 +116,11 @@ struct hrg_job {
     int64_t old_entries = 0;
 };
 
+// The write pass of hrg_generate_host runs in up to kMaxChunks id ranges, so
+// that each range's neighbour ids go back to the host while the next range
+// is written and sorted.
+constexpr int kMaxChunks = 8;
+
 struct hrg_ctx {
     int device = 0;
     std::string err;
@@ -125,11 +131,14 @@ struct hrg_ctx {
            W_HUBOFF, W_HUBPOS, W_WARPCNT, W_SEGCNT, W_POSOF, W_RELIST0, W_RELIST1, W_RELIST2, W_RELIST3,
            W_PACC, W_POUTDEG, W_POUTOFF, W_POUTCOL, W_PTRI, W_PSCAN, W_LRCNT, W_LROFF, W_LRLIST, W_LRFIN,
            W_LRDEG, W_HPOOL, W_HRUNS, W_HPCUR, W_BFSF0, W_BFSF1, W_BFSDEG, W_BFSOFF, W_BFSACC, W_BFSDIST,
-           W_MVBITS, W_MVREM, W_MVADD, W_MVCUR, W_MVKEEP, W_MVERR, W_MVSTART, W_MVWS, W_COUNT };
+           W_MVBITS, W_MVREM, W_MVADD, W_MVCUR, W_MVKEEP, W_MVERR, W_MVSTART, W_MVWS, W_CHUNK, W_COUNT };
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
     cudaEvent_t ev[10] = {};  // stage boundaries of the current job
     cudaStream_t work = nullptr, copy = nullptr;  // hrg_generate_host: generation and read-back streams
+    // hrg_generate_host: [0] points sampled, [1] [2] first and last read-back
+    // on the copy stream, then four per range of the chunked write pass
+    cudaEvent_t hev[3 + 4 * kMaxChunks] = {};
     hrg_job job;
     hrg_limits lim{};  // capacities of the count pass's buffers (0: automatic)
     std::vector<Plan> batch_plans;  // host plans of the current batch
@@ -232,6 +241,8 @@ extern "C" int hrg_destroy(hrg_ctx *ctx)
     if (ctx->work) cudaStreamDestroy(ctx->work);
     if (ctx->copy) cudaStreamDestroy(ctx->copy);
     for (auto &ev : ctx->ev)
+        if (ev) cudaEventDestroy(ev);
+    for (auto &ev : ctx->hev)
         if (ev) cudaEventDestroy(ev);
     delete ctx;
     return HRG_OK;
@@ -516,10 +527,18 @@ static void expected_band_counts(const Plan &p, int64_t *cnt)
     }
 }
 
+// hrg_generate_host: the sampled points go back to these host buffers on
+// the copy stream as soon as the sampler has written them.
+struct HostPoints {
+    double *r_host, *phi_host;
+    cudaStream_t copy;
+    cudaEvent_t sampled, copy_start;
+};
+
 static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params *prm, int64_t n, double R,
                         double alpha, const double *r_in, const double *phi_in, double *r_out, double *phi_out,
                         uint32_t flags, int32_t bands, cudaStream_t st, int64_t *row_off_out, int64_t *n_entries,
-                        bool count_pass = true)
+                        bool count_pass = true, const HostPoints *hpts = nullptr)
 {
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
     J = hrg_job();
@@ -570,6 +589,13 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
         J.r = r_out;
         J.phi = phi_out;
         CK(cudaEventRecord(ctx->ev[1], st));
+        if (hpts) {
+            CK(cudaEventRecord(hpts->sampled, st));
+            CK(cudaStreamWaitEvent(hpts->copy, hpts->sampled, 0));
+            CK(cudaEventRecord(hpts->copy_start, hpts->copy));
+            CK(cudaMemcpyAsync(hpts->r_host, r_out, sizeof(double) * n, cudaMemcpyDeviceToHost, hpts->copy));
+            CK(cudaMemcpyAsync(hpts->phi_host, phi_out, sizeof(double) * n, cudaMemcpyDeviceToHost, hpts->copy));
+        }
         CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));
     } else {
         CK(launch_count_bands(p, r_in, phi_in, (int64_t *)band_cnt, st));
@@ -629,8 +655,8 @@ static int check_params(hrg_ctx *ctx, const hrg_params *p, double *R)
     return HRG_OK;
 }
 
-extern "C" int hrg_generate_begin(hrg_ctx *ctx, const hrg_params *p, void *stream, double *r_out, double *phi_out,
-                                  int64_t *row_off_out, hrg_job **job, int64_t *n_entries)
+static int generate_begin(hrg_ctx *ctx, const hrg_params *p, void *stream, double *r_out, double *phi_out,
+                          int64_t *row_off_out, hrg_job **job, int64_t *n_entries, const HostPoints *hpts)
 {
     if (!ctx) return HRG_EINVAL;
     if (!job || !n_entries || !r_out || !phi_out || !row_off_out) return set_err(ctx, HRG_EINVAL, "null argument");
@@ -639,13 +665,19 @@ extern "C" int hrg_generate_begin(hrg_ctx *ctx, const hrg_params *p, void *strea
     int rc = check_params(ctx, p, &R);
     if (rc) return rc;
     rc = begin_common(ctx, ctx->job, true, p, p->n, R, p->alpha, nullptr, nullptr, r_out, phi_out, p->flags,
-                      p->bands, (cudaStream_t)stream, row_off_out, n_entries);
+                      p->bands, (cudaStream_t)stream, row_off_out, n_entries, true, hpts);
     if (rc) {
         ctx->job.open = false;
         return rc;
     }
     *job = &ctx->job;
     return HRG_OK;
+}
+
+extern "C" int hrg_generate_begin(hrg_ctx *ctx, const hrg_params *p, void *stream, double *r_out, double *phi_out,
+                                  int64_t *row_off_out, hrg_job **job, int64_t *n_entries)
+{
+    return generate_begin(ctx, p, stream, r_out, phi_out, row_off_out, job, n_entries, nullptr);
 }
 
 extern "C" int hrg_generate_from_points_begin(hrg_ctx *ctx, int64_t n, double R, const double *r, const double *phi,
@@ -1016,6 +1048,143 @@ static int update_finish(hrg_job *job, int32_t *col_out)
     return HRG_OK;
 }
 
+// hrg_generate_host: the neighbour ids go back to this host buffer, range by
+// range, on the copy stream.
+struct HostCol {
+    int32_t *col_host;
+    cudaStream_t copy;
+};
+
+// Ranges of the chunked write pass: about 2e8 entries each, at most
+// kMaxChunks, and none below 2^26 entries in all (a single range then).
+static int write_chunks(const hrg_job *job)
+{
+    if (!job->hub_pooled || job->batch || job->n_entries < ((int64_t)1 << 26)) return 1;
+    return (int)std::min<int64_t>(kMaxChunks, std::max<int64_t>(2, job->n_entries / 200000000));
+}
+
+static int finish_impl(hrg_job *job, int32_t *col_idx_out, const HostCol *hc)
+{
+    hrg_ctx *ctx = job->ctx;
+    if (job->update) return update_finish(job, col_idx_out);
+    cudaStream_t st = job->stream;
+    const Plan &p = job->plan;
+    const int64_t n = p.n;
+    const int K = hc ? write_chunks(job) : 1;
+    job->write_chunks = K;
+    int rc;
+    void *tmp = nullptr, *bws = nullptr;
+    if (job->lists[2] > 0) {
+        if ((rc = ensure(ctx, hrg_ctx::W_TMP, sizeof(int32_t) * job->big_total, &tmp))) return rc;
+        if ((rc = ensure(ctx, hrg_ctx::W_BUCKET, big_sort_ws_bytes(job->lists[2], job->big_total), &bws))) return rc;
+    }
+    // Range k holds the ids [bounds[k], bounds[k+1]) (multiples of 32) and the
+    // entries [offs[k], offs[k+1]); the sort lists are split by range.
+    int64_t bounds[kMaxChunks + 1], offs[kMaxChunks + 1];
+    int32_t sub_cnt[3 * kMaxChunks] = {};
+    int64_t sub_tot[kMaxChunks] = {};
+    int32_t *sub = nullptr, *dsub_cnt = nullptr;
+    if (K > 1) {
+        for (int k = 0; k < K; ++k) bounds[k] = ((n * k / K) >> 5) << 5;
+        bounds[K] = n;
+        const int64_t lsum = (int64_t)job->lists[0] + job->lists[1] + job->lists[2];
+        const size_t b_bounds = 64 * 2, b_cnt = 256, b_tot = 64 * 2;
+        void *w;
+        if ((rc = ensure(ctx, hrg_ctx::W_CHUNK, b_bounds + b_cnt + b_tot + sizeof(int32_t) * (K * lsum + 1), &w)))
+            return rc;
+        int64_t *dbounds = (int64_t *)w;
+        dsub_cnt = (int32_t *)((char *)w + b_bounds);
+        int64_t *dsub_tot = (int64_t *)((char *)w + b_bounds + b_cnt);
+        sub = (int32_t *)((char *)w + b_bounds + b_cnt + b_tot);
+        char *hp = (char *)ctx->pinned;
+        memcpy(hp, bounds, sizeof(int64_t) * (K + 1));
+        CK(cudaMemcpyAsync(dbounds, hp, sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(dsub_cnt, 0, b_cnt + b_tot, st));
+        CK(launch_split_lists(job->qb, job->lists, K, dbounds, job->row_off, sub, dsub_cnt, dsub_tot, st));
+        CK(cudaMemcpyAsync(hp + 256, dsub_cnt, sizeof(int32_t) * 3 * K, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hp + 512, dsub_tot, sizeof(int64_t) * K, cudaMemcpyDeviceToHost, st));
+        for (int k = 0; k <= K; ++k)
+            CK(cudaMemcpyAsync(hp + 768 + 8 * k, job->row_off + bounds[k], sizeof(int64_t), cudaMemcpyDeviceToHost,
+                               st));
+        CK(cudaStreamSynchronize(st));
+        memcpy(sub_cnt, hp + 256, sizeof(int32_t) * 3 * K);
+        memcpy(sub_tot, hp + 512, sizeof(int64_t) * K);
+        memcpy(offs, hp + 768, sizeof(int64_t) * (K + 1));
+    } else {
+        bounds[0] = 0;
+        bounds[1] = n;
+        offs[0] = 0;
+        offs[1] = job->n_entries;
+        for (int c = 0; c < 3; ++c) sub_cnt[c] = job->lists[c];
+        sub_tot[0] = job->big_total;
+    }
+    cudaEvent_t *cev = ctx->hev + 3;
+    CK(cudaEventRecord(ctx->ev[6], st));
+    if (job->p_hub > 0) CK(cudaMemsetAsync(job->qb.cursor, 0, sizeof(int32_t) * job->p_hub, st));
+    for (int k = 0; k < K; ++k) {
+        const int64_t lo = bounds[k], hi = bounds[k + 1];
+        if (K > 1) CK(cudaEventRecord(cev[4 * k + 0], st));
+        if (job->hub_pooled)
+            CK(launch_copy_hub(job->qb, job->p_hub, job->hub_runs, job->row_off, col_idx_out, lo, hi, k == K - 1,
+                               st));
+        else
+            CK(launch_write_hub(p, job->qb, job->fp64, job->p_hub, job->row_off, col_idx_out, st));
+        CK(cudaEventRecord(K > 1 ? cev[4 * k + 1] : ctx->ev[7], st));
+        CK(launch_write_rim(p, job->qb, job->fp64, job->row_off, col_idx_out, lo, hi, st));
+        CK(cudaEventRecord(K > 1 ? cev[4 * k + 2] : ctx->ev[8], st));
+        const int32_t *cnt = sub_cnt + 3 * k;
+        if (cnt[0] > 0 || cnt[1] > 0 || cnt[2] > 0) {
+            QueryBufs bc = job->qb;
+            if (K > 1) {
+                int64_t off = 0;
+                for (int c = 0; c < 3; ++c) {
+                    bc.rows[c] = sub + off + (int64_t)k * job->lists[c];
+                    off += (int64_t)K * job->lists[c];
+                }
+                bc.list_cnt = dsub_cnt + 3 * k;
+            }
+            CK(launch_sort_rows(p, bc, cnt, sub_tot[k], job->row_off, col_idx_out, (int32_t *)tmp, bws, st));
+        }
+        if (K > 1) CK(cudaEventRecord(cev[4 * k + 3], st));
+        if (hc && offs[k + 1] > offs[k]) {
+            cudaEvent_t done = K > 1 ? cev[4 * k + 3] : ctx->hev[0];
+            if (K == 1) CK(cudaEventRecord(done, st));
+            CK(cudaStreamWaitEvent(hc->copy, done, 0));
+            CK(cudaMemcpyAsync(hc->col_host + offs[k], col_idx_out + offs[k], sizeof(int32_t) * (offs[k + 1] - offs[k]),
+                               cudaMemcpyDeviceToHost, hc->copy));
+        }
+    }
+    CK(cudaEventRecord(ctx->ev[9], st));
+    uint64_t *hs = (uint64_t *)ctx->pinned;
+    CK(cudaMemcpyAsync(hs, job->qb.stats + 7, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    job->finished = true;
+    auto elapsed = [](cudaEvent_t a, cudaEvent_t b) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+            cudaGetLastError();
+            ms = -1.0f;
+        }
+        return ms;
+    };
+    const int pairs[5][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}};
+    for (int k = 0; k < 5; ++k) job->stage_ms[k] = elapsed(ctx->ev[pairs[k][0]], ctx->ev[pairs[k][1]]);
+    if (K > 1) {
+        // the write stages summed over the ranges
+        for (int j = 0; j < 3; ++j) {
+            float t = 0.0f;
+            for (int k = 0; k < K; ++k) t += elapsed(cev[4 * k + j], cev[4 * k + j + 1]);
+            job->stage_ms[5 + j] = t;
+        }
+    } else {
+        job->stage_ms[5] = elapsed(ctx->ev[6], ctx->ev[7]);
+        job->stage_ms[6] = elapsed(ctx->ev[7], ctx->ev[8]);
+        job->stage_ms[7] = elapsed(ctx->ev[8], ctx->ev[9]);
+    }
+    if (hs[0] != 0) return set_err(ctx, HRG_EINTERNAL, "count and write passes disagree on a row");
+    return HRG_OK;
+}
+
 extern "C" int hrg_generate_finish(hrg_job *job, int32_t *col_idx_out)
 {
     if (!job || !job->ctx) return HRG_EINVAL;
@@ -1023,45 +1192,7 @@ extern "C" int hrg_generate_finish(hrg_job *job, int32_t *col_idx_out)
     if (!job->open || job->finished) return set_err(ctx, HRG_ESTATE, "job is not open");
     if (!col_idx_out && job->n_entries > 0) return set_err(ctx, HRG_EINVAL, "null col_idx");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
-    if (job->update) return update_finish(job, col_idx_out);
-    cudaStream_t st = job->stream;
-    const Plan &p = job->plan;
-    CK(cudaEventRecord(ctx->ev[6], st));
-    if (job->p_hub > 0) CK(cudaMemsetAsync(job->qb.cursor, 0, sizeof(int32_t) * job->p_hub, st));
-    if (job->hub_pooled)
-        CK(launch_copy_hub(job->qb, job->p_hub, job->hub_runs, job->row_off, col_idx_out, st));
-    else
-        CK(launch_write_hub(p, job->qb, job->fp64, job->p_hub, job->row_off, col_idx_out, st));
-    CK(cudaEventRecord(ctx->ev[7], st));
-    CK(launch_write_rim(p, job->qb, job->fp64, job->row_off, col_idx_out, st));
-    CK(cudaEventRecord(ctx->ev[8], st));
-    if (job->lists[0] > 0 || job->lists[1] > 0 || job->lists[2] > 0) {
-        void *tmp = nullptr, *bws = nullptr;
-        int rc;
-        if (job->lists[2] > 0) {
-            if ((rc = ensure(ctx, hrg_ctx::W_TMP, sizeof(int32_t) * job->big_total, &tmp))) return rc;
-            if ((rc = ensure(ctx, hrg_ctx::W_BUCKET, big_sort_ws_bytes(job->lists[2], job->big_total), &bws)))
-                return rc;
-        }
-        CK(launch_sort_rows(p, job->qb, job->lists, job->big_total, job->row_off, col_idx_out, (int32_t *)tmp, bws,
-                            st));
-    }
-    CK(cudaEventRecord(ctx->ev[9], st));
-    uint64_t *hs = (uint64_t *)ctx->pinned;
-    CK(cudaMemcpyAsync(hs, job->qb.stats + 7, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    job->finished = true;
-    const int pairs[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {6, 7}, {7, 8}, {8, 9}};
-    for (int k = 0; k < 8; ++k) {
-        float ms = 0.0f;
-        if (cudaEventElapsedTime(&ms, ctx->ev[pairs[k][0]], ctx->ev[pairs[k][1]]) != cudaSuccess) {
-            cudaGetLastError();
-            ms = -1.0f;
-        }
-        job->stage_ms[k] = ms;
-    }
-    if (hs[0] != 0) return set_err(ctx, HRG_EINTERNAL, "count and write passes disagree on a row");
-    return HRG_OK;
+    return finish_impl(job, col_idx_out, nullptr);
 }
 
 extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
@@ -1080,6 +1211,8 @@ extern "C" int hrg_job_stats(const hrg_job *job, hrg_stats *out)
     out->big_rows = job->lists[2];
     out->mu = job->plan.mu;
     for (int k = 0; k < 8; ++k) out->stage_ms[k] = job->stage_ms[k];
+    out->write_chunks = job->write_chunks;
+    out->d2h_ms = -1.0f;
     out->ties = job->stats[3];
     out->rows_no_room = (int64_t)job->stats[4];
     out->hub_rows_retraversed = (job->p_hub > 0 && !job->hub_pooled) ? job->p_hub : 0;
@@ -1169,6 +1302,8 @@ extern "C" int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_ho
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, HRG_ECUDA, "cudaSetDevice failed");
     if (!ctx->work) CK(cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking));
     if (!ctx->copy) CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+    for (auto &ev : ctx->hev)
+        if (!ev) CK(cudaEventCreate(&ev));
     const int64_t n = p->n;
     void *dr, *dphi, *doff, *dcol;
     int rc;
@@ -1178,35 +1313,46 @@ extern "C" int hrg_generate_host(hrg_ctx *ctx, const hrg_params *p, double *r_ho
     hrg_job *job = nullptr;
     int64_t ne = 0;
     cudaStream_t st = ctx->work, cp = ctx->copy;
-    rc = hrg_generate_begin(ctx, p, st, (double *)dr, (double *)dphi, (int64_t *)doff, &job, &ne);
-    if (rc) return rc;
+    // the points go back while the graph is generated (from the sampler
+    // on), the row offsets once they are known, the neighbour ids range by
+    // range as the write pass finishes each
+    const HostPoints hpts{r_host, phi_host, cp, ctx->hev[0], ctx->hev[1]};
+    rc = generate_begin(ctx, p, st, (double *)dr, (double *)dphi, (int64_t *)doff, &job, &ne, &hpts);
+    if (rc) {
+        cudaStreamSynchronize(cp);
+        return rc;
+    }
     *n_entries = ne;
     if (ne > col_capacity || (ne > 0 && !col_idx_host)) {
         if (stats_out) hrg_job_stats(job, stats_out);
         hrg_job_release(job);
+        cudaStreamSynchronize(cp);
         return set_err(ctx, HRG_EOVERFLOW, "graph has %lld entries, capacity %lld", (long long)ne,
                        (long long)col_capacity);
     }
     if ((rc = ensure(ctx, hrg_ctx::W_OUT_COL, sizeof(int32_t) * (ne > 0 ? ne : 1), &dcol))) {
         hrg_job_release(job);
-        return rc;
-    }
-    // begin has synchronized the generation stream: the points and row
-    // offsets are final, so they go back to the host while the neighbour
-    // ids are written and sorted
-    CK(cudaMemcpyAsync(r_host, dr, sizeof(double) * n, cudaMemcpyDeviceToHost, cp));
-    CK(cudaMemcpyAsync(phi_host, dphi, sizeof(double) * n, cudaMemcpyDeviceToHost, cp));
-    CK(cudaMemcpyAsync(row_off_host, doff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, cp));
-    rc = hrg_generate_finish(job, (int32_t *)dcol);
-    if (stats_out) hrg_job_stats(job, stats_out);
-    hrg_job_release(job);
-    if (rc) {
         cudaStreamSynchronize(cp);
         return rc;
     }
-    if (ne > 0) CK(cudaMemcpyAsync(col_idx_host, dcol, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    CK(cudaStreamSynchronize(cp));
+    // begin has synchronized the generation stream: the row offsets are final
+    CK(cudaMemcpyAsync(row_off_host, doff, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, cp));
+    const HostCol hcol{col_idx_host, cp};
+    rc = finish_impl(job, (int32_t *)dcol, &hcol);
+    CK(cudaEventRecord(ctx->hev[2], cp));
+    const cudaError_t ce = cudaStreamSynchronize(cp);
+    if (stats_out) {
+        hrg_job_stats(job, stats_out);
+        float ms = -1.0f;
+        if (ce == cudaSuccess && cudaEventElapsedTime(&ms, ctx->hev[1], ctx->hev[2]) != cudaSuccess) {
+            cudaGetLastError();
+            ms = -1.0f;
+        }
+        stats_out->d2h_ms = ms;
+    }
+    hrg_job_release(job);
+    if (rc) return rc;
+    if (ce != cudaSuccess) return set_err(ctx, HRG_ECUDA, "read-back failed: %s", cudaGetErrorString(ce));
     return HRG_OK;
 }
 

@@ -174,16 +174,18 @@ cudaError_t launch_count_rim(const Plan &p, const QueryBufs &b, bool fp64_only, 
 // Same traversals, writing neighbour ids into col_idx[row_off[id] ..]; hub
 // rows are written in no particular order (sorted later): the query's warp
 // first, then its heavy segments, each at an offset reserved with one atomic.
-// The hub rows from the pooled runs (one atomic per run on the row's cursor,
-// cursor zeroed by the caller), then the cursors checked against the degrees.
+// The hub rows of ids [lo, hi) from the pooled runs (one atomic per run on
+// the row's cursor, cursor zeroed by the caller); check: then every hub row's
+// cursor checked against its degree (after the last range).
 cudaError_t launch_copy_hub(const QueryBufs &b, int32_t p_hub, int32_t n_runs, const int64_t *row_off,
-                            int32_t *col_idx, cudaStream_t s);
+                            int32_t *col_idx, int64_t lo, int64_t hi, bool check, cudaStream_t s);
 cudaError_t launch_write_hub(const Plan &p, const QueryBufs &b, bool fp64_only, int32_t p_hub,
                              const int64_t *row_off, int32_t *col_idx, cudaStream_t s);
-// Rim rows: kept rows are copied (those of up to kCopySortRow entries sorted
-// on the way), the others traversed again.
+// Rim rows of ids [lo, hi) (lo a multiple of 32): kept rows are copied
+// (those of up to kCopySortRow entries sorted on the way), the others
+// traversed again.
 cudaError_t launch_write_rim(const Plan &p, const QueryBufs &b, bool fp64_only, const int64_t *row_off,
-                             int32_t *col_idx, cudaStream_t s);
+                             int32_t *col_idx, int64_t lo, int64_t hi, cudaStream_t s);
 int query_launches(const Plan &p, int32_t p_hub, bool write);
 // Moved vertices of a dynamic update: one CTA per id in ids[k] queries its
 // position in the band structure.  Count (write = false): deg[u] = new
@@ -230,5 +232,13 @@ size_t big_sort_ws_bytes(int n_big, int64_t big_total);
 int sort_launches(const int32_t counts[3]);
 cudaError_t launch_sort_rows(const Plan &p, const QueryBufs &b, const int32_t counts[3], int64_t big_total,
                              const int64_t *row_off, int32_t *col_idx, int32_t *tmp, void *ws, cudaStream_t s);
+// The three sort lists split by id range: range k = [bounds[k], bounds[k+1])
+// of K ranges.  Class c's rows of range k go to sub + off_c + k cap_c (off_c
+// = K (cap_0 + ... + cap_{c-1}), cap_c = counts[c]), their number to
+// sub_cnt[3 k + c] and, for class 2, their degree sum to sub_tot[k]
+// (sub_cnt and sub_tot zeroed by the caller).
+cudaError_t launch_split_lists(const QueryBufs &b, const int32_t counts[3], int K, const int64_t *bounds,
+                               const int64_t *row_off, int32_t *sub, int32_t *sub_cnt, int64_t *sub_tot,
+                               cudaStream_t s);
 
 }  // namespace hrg

@@ -489,16 +489,17 @@ __device__ __forceinline__ void sort_tile_row(int32_t (*T)[kRegRow + 1], const i
         if (j < deg) T[lane][j] = v[j] - off;
 }
 
+// Ids [lo, hi) only (lo a multiple of 32).
 template <bool BATCH>
 __global__ void __launch_bounds__(32 * kCopyWarps) k_rim_copy(Plan p, QueryBufs b, const int64_t *__restrict__ row_off,
-                                                              int32_t *__restrict__ col_idx)
+                                                              int32_t *__restrict__ col_idx, int64_t lo, int64_t hi)
 {
     __shared__ int32_t tile[kCopyWarps][kRegRow][kRegRow + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int32_t(*T)[kRegRow + 1] = tile[w];
-    const int64_t n = p.n, groups = (n + 31) >> 5;
+    const int64_t n = hi, groups = (hi + 31) >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * kCopyWarps;
-    for (int64_t t = (int64_t)blockIdx.x * kCopyWarps + w; t < groups; t += nwarps) {
+    for (int64_t t = (lo >> 5) + (int64_t)blockIdx.x * kCopyWarps + w; t < groups; t += nwarps) {
         const int64_t id = (t << 5) + lane;
         int32_t stored = -1, deg = 0, off = 0;
         int64_t base = 0;
@@ -559,16 +560,22 @@ __global__ void __launch_bounds__(32 * kCopyWarps) k_rim_copy(Plan p, QueryBufs 
 
 // Rows the count pass did not keep (longer than kRegRow, or no room): the
 // traversal again, one thread per row, all such rows side by side.
+// Rows of ids [lo, hi) only.
 template <bool F64, bool BATCH>
 __global__ void __launch_bounds__(256) k_rim_relist(Plan p, QueryBufs b, const int64_t *__restrict__ row_off,
-                                                    int32_t *__restrict__ col_idx)
+                                                    int32_t *__restrict__ col_idx, int64_t lo, int64_t hi)
 {
     const int cls = blockIdx.y;
     const int32_t nr = *((volatile int32_t *)&b.list_cnt[4 + cls]);
     const int32_t *relist = b.relist[cls];
     unsigned n_cand = 0, n_re = 0, n_edge = 0;
+    const bool all = lo == 0 && hi >= p.n;
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
         const int32_t qp = relist[k];
+        if (!all) {
+            const int32_t id = b.pms[qp].id;
+            if (id < lo || id >= hi) continue;
+        }
         if (BATCH)
             thread_query<F64, true>(b.plans[__ldg(b.graph_of + qp)], b, qp, true, row_off, col_idx, n_cand, n_re,
                                     n_edge);
@@ -919,8 +926,9 @@ __global__ void k_hub_check(QueryBufs b, int32_t p_hub)
 
 // Write pass from the pool: one warp per run; its place in the row comes from
 // one atomic on the row's cursor.
+// Runs of the rows of ids [lo, hi) only.
 __global__ void __launch_bounds__(256) k_hub_copy(QueryBufs b, int32_t n_runs, const int64_t *__restrict__ row_off,
-                                                  int32_t *__restrict__ col_out)
+                                                  int32_t *__restrict__ col_out, int64_t lo, int64_t hi)
 {
     const int lane = threadIdx.x & 31;
     const int32_t nwarps = (int32_t)(gridDim.x * (blockDim.x >> 5));
@@ -928,12 +936,13 @@ __global__ void __launch_bounds__(256) k_hub_copy(QueryBufs b, int32_t n_runs, c
         const int4 run = b.runs[k];
         const int32_t qi = run.x, cnt = run.y;
         const unsigned long long off = ((unsigned long long)(uint32_t)run.w << 32) | (unsigned long long)(uint32_t)run.z;
-        int64_t dst = 0;
+        int64_t dst = -1;
         if (lane == 0) {
             const int32_t id = b.pms[hub_position(b, qi)].id;
-            dst = row_off[id] + atomicAdd(&b.cursor[qi], cnt);
+            if (id >= lo && id < hi) dst = row_off[id] + atomicAdd(&b.cursor[qi], cnt);
         }
         dst = __shfl_sync(0xffffffffu, dst, 0);
+        if (dst < 0) continue;
         for (int32_t t = lane; t < cnt; t += 32) col_out[dst + t] = b.pool[off + t];
     }
 }
@@ -986,18 +995,19 @@ static void rim_count_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only
 }
 
 static void rim_write_dispatch(const Plan &p, const QueryBufs &b, bool fp64_only, const int64_t *row_off,
-                               int32_t *col_idx, cudaStream_t s)
+                               int32_t *col_idx, int64_t lo, int64_t hi, cudaStream_t s)
 {
     const bool batch = b.plans != nullptr;
     const unsigned cg = kRimWriteGrid / 2;
-    if (batch) k_rim_copy<true><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
-    else k_rim_copy<false><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx);
+    const dim3 rg(kRimWriteGrid / 4, 4);
+    if (batch) k_rim_copy<true><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx, lo, hi);
+    else k_rim_copy<false><<<cg, 32 * kCopyWarps, 0, s>>>(p, b, row_off, col_idx, lo, hi);
     if (fp64_only) {
-        if (batch) k_rim_relist<true, true><<<dim3(kRimWriteGrid / 4, 4), 256, 0, s>>>(p, b, row_off, col_idx);
-        else k_rim_relist<true, false><<<dim3(kRimWriteGrid / 4, 4), 256, 0, s>>>(p, b, row_off, col_idx);
+        if (batch) k_rim_relist<true, true><<<rg, 256, 0, s>>>(p, b, row_off, col_idx, lo, hi);
+        else k_rim_relist<true, false><<<rg, 256, 0, s>>>(p, b, row_off, col_idx, lo, hi);
     } else {
-        if (batch) k_rim_relist<false, true><<<dim3(kRimWriteGrid / 4, 4), 256, 0, s>>>(p, b, row_off, col_idx);
-        else k_rim_relist<false, false><<<dim3(kRimWriteGrid / 4, 4), 256, 0, s>>>(p, b, row_off, col_idx);
+        if (batch) k_rim_relist<false, true><<<rg, 256, 0, s>>>(p, b, row_off, col_idx, lo, hi);
+        else k_rim_relist<false, false><<<rg, 256, 0, s>>>(p, b, row_off, col_idx, lo, hi);
     }
 }
 
@@ -1115,11 +1125,11 @@ cudaError_t launch_count_hub(const Plan &p, const QueryBufs &b, bool fp64_only, 
 }
 
 cudaError_t launch_copy_hub(const QueryBufs &b, int32_t p_hub, int32_t n_runs, const int64_t *row_off,
-                            int32_t *col_idx, cudaStream_t s)
+                            int32_t *col_idx, int64_t lo, int64_t hi, bool check, cudaStream_t s)
 {
     if (p_hub <= 0) return cudaSuccess;
-    if (n_runs > 0) k_hub_copy<<<kRimWriteGrid / 2, 256, 0, s>>>(b, n_runs, row_off, col_idx);
-    k_hub_check_pooled<<<(unsigned)((p_hub + 255) / 256), 256, 0, s>>>(b, p_hub);
+    if (n_runs > 0) k_hub_copy<<<kRimWriteGrid / 2, 256, 0, s>>>(b, n_runs, row_off, col_idx, lo, hi);
+    if (check) k_hub_check_pooled<<<(unsigned)((p_hub + 255) / 256), 256, 0, s>>>(b, p_hub);
     return cudaGetLastError();
 }
 
@@ -1160,11 +1170,11 @@ cudaError_t launch_count_rim(const Plan &p, const QueryBufs &b, bool fp64_only, 
 }
 
 cudaError_t launch_write_rim(const Plan &p, const QueryBufs &b, bool fp64_only, const int64_t *row_off,
-                             int32_t *col_idx, cudaStream_t s)
+                             int32_t *col_idx, int64_t lo, int64_t hi, cudaStream_t s)
 {
     if (b.plans == nullptr && p.hub_bands >= p.B) return cudaSuccess;
     if (b.plans != nullptr && b.n_sectors == 0) return cudaSuccess;
-    rim_write_dispatch(p, b, fp64_only, row_off, col_idx, s);
+    rim_write_dispatch(p, b, fp64_only, row_off, col_idx, lo, hi, s);
     return cudaGetLastError();
 }
 

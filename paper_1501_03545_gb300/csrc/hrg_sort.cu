@@ -509,7 +509,46 @@ __global__ void __launch_bounds__(1024) k_sort_slow(const Item *__restrict__ ite
     }
 }
 
+// One thread per entry of the three lists: its range by a search over the
+// (few) bounds, then an append to that range's part of its class.
+__global__ void k_split_lists(const int32_t *__restrict__ l0, const int32_t *__restrict__ l1,
+                              const int32_t *__restrict__ l2, int32_t c0, int32_t c1, int32_t c2, int K,
+                              const int64_t *__restrict__ bounds, const int64_t *__restrict__ row_off,
+                              int32_t *__restrict__ sub, int32_t *__restrict__ sub_cnt, int64_t *__restrict__ sub_tot)
+{
+    const int64_t total = (int64_t)c0 + c1 + c2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int cls;
+        int32_t id, cap;
+        int64_t base;
+        if (t < c0) {
+            cls = 0; id = l0[t]; cap = c0; base = 0;
+        } else if (t < (int64_t)c0 + c1) {
+            cls = 1; id = l1[t - c0]; cap = c1; base = (int64_t)K * c0;
+        } else {
+            cls = 2; id = l2[t - c0 - c1]; cap = c2; base = (int64_t)K * (c0 + c1);
+        }
+        int k = 0;
+        while (k + 1 < K && __ldg(bounds + k + 1) <= id) ++k;
+        const int32_t slot = atomicAdd(&sub_cnt[3 * k + cls], 1);
+        sub[base + (int64_t)k * cap + slot] = id;
+        if (cls == 2) atomicAdd((unsigned long long *)&sub_tot[k], (unsigned long long)(row_off[id + 1] - row_off[id]));
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_split_lists(const QueryBufs &b, const int32_t counts[3], int K, const int64_t *bounds,
+                               const int64_t *row_off, int32_t *sub, int32_t *sub_cnt, int64_t *sub_tot,
+                               cudaStream_t s)
+{
+    const int64_t total = (int64_t)counts[0] + counts[1] + counts[2];
+    if (total == 0) return cudaSuccess;
+    const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
+    k_split_lists<<<g, 256, 0, s>>>(b.rows[0], b.rows[1], b.rows[2], counts[0], counts[1], counts[2], K, bounds,
+                                   row_off, sub, sub_cnt, sub_tot);
+    return cudaGetLastError();
+}
 
 size_t sort_smem_bytes() { return sizeof(SortSmem); }
 

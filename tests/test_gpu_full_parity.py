@@ -6,7 +6,9 @@ full, in the launch configuration the benchmark times:
 * it equals, entry for entry, the CSR of the oracle's band algorithm on the
   host cores, outside the oracle's tie band (pairs within 1e-12 cosh R of
   the threshold), whose size the device reports the same;
-* every angle is bit-identical and every radius within 8 ulp of the oracle's.
+* every angle is bit-identical and every radius within 8 ulp of the oracle's;
+* the host-buffer entry point (its write pass in 8 id ranges) returns the
+  same arrays.
 
 The oracle side takes a few minutes on the host cores; the time of each part
 is printed (run with -s to see it).
@@ -77,6 +79,18 @@ def test_large_workload_full_csr_against_oracle_and_fp64_path():
         g_off, g_col = a["row_off"].cpu().numpy(), a["col_idx"].cpu().numpy()
         del a
         torch.cuda.empty_cache()
+        # the host-buffer entry point (the write pass in id ranges, each copied
+        # back while the next is written) gives the same arrays
+        n, ne = w.n, int(g_off[-1])
+        rh = torch.empty(n, dtype=torch.float64).pin_memory()
+        ph = torch.empty(n, dtype=torch.float64).pin_memory()
+        oh = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+        ch = torch.empty(ne, dtype=torch.int32).pin_memory()
+        got, sth = H.generate_host(ctx, n, w.alpha, w.kbar, w.seed, rh, ph, oh, ch)
+        assert got == ne and sth["write_chunks"] == 8
+        assert np.array_equal(rh.numpy(), g_r) and np.array_equal(ph.numpy(), g_phi)
+        assert np.array_equal(oh.numpy(), g_off) and np.array_equal(ch.numpy(), g_col)
+        del rh, ph, oh, ch
     finally:
         ctx.close()
     _log("device: two generations, FP32 = FP64 compare and copies in %.1f s; %d entries, %d candidates, "

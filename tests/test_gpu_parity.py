@@ -266,6 +266,28 @@ def test_host_entry_point_matches_device(ctx):
     assert e.value.code == H.HRG_EOVERFLOW
 
 
+def test_host_entry_point_in_ranges_matches_device(ctx):
+    # 8e7 entries: the write pass runs in two id ranges, the first copied
+    # back while the second is written and sorted
+    w = W.scaled(W.LARGE, 5_000_000)
+    d = gen(ctx, w)
+    n = w.n
+    ne = int(d["row_off"][-1])
+    assert ne >= 1 << 26
+    rh = torch.empty(n, dtype=torch.float64).pin_memory()
+    ph = torch.empty(n, dtype=torch.float64).pin_memory()
+    oh = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+    ch = torch.empty(ne + 100, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        ch.fill_(-1)
+        got, st = H.generate_host(ctx, n, w.alpha, w.kbar, w.seed, rh, ph, oh, ch)
+        assert got == ne and st["write_chunks"] == 2 and st["d2h_ms"] > 0
+        assert torch.equal(rh, d["r"].cpu()) and torch.equal(ph, d["phi"].cpu())
+        assert torch.equal(oh, d["row_off"].cpu()) and torch.equal(ch[:ne], d["col_idx"].cpu())
+        assert bool((ch[ne:] == -1).all())
+        assert sum(st["stage_ms"].values()) > 0
+
+
 def test_error_codes(ctx):
     with pytest.raises(H.HrgError) as e:
         H.generate(ctx, 1000, 0.5, 5.0, 1)
