@@ -213,7 +213,7 @@ __device__ __forceinline__ void warp_append(int32_t *list, int32_t *count, bool 
     if (e) list[base + __popc(m & ((1u << lane) - 1u))] = v;
 }
 
-constexpr int kRimThreads = 256;
+constexpr int kRimThreads = 128;
 
 // ---------------------------------------------------------------------------
 // One query, one thread (rim bands).  The count pass stores a row of up to
@@ -438,16 +438,22 @@ __device__ __forceinline__ void rim_sector(const Plan &p, const QueryBufs &b, in
         s_pre[j + 1] = e - s;
     }
     __syncthreads();
+    __shared__ int32_t s_next;
     if (threadIdx.x == 0) {
         s_pre[0] = 0;
         for (int j = 0; j < HRG_MAX_BANDS; ++j) s_pre[j + 1] += s_pre[j];
+        s_next = blockDim.x;
     }
     __syncthreads();
     const int32_t total = s_pre[HRG_MAX_BANDS];
     unsigned n_cand = 0, n_re = 0, n_edge = 0;
     int j = 0;
-    // warp-uniform loop (the count pass reserves buffer space per warp)
-    for (int32_t t0 = threadIdx.x & ~31; t0 < total; t0 += blockDim.x) {
+    // Warp-uniform loop (the count pass reserves buffer space per warp):
+    // warp w takes the 32 queries from 32 w first, then the next 32 not yet
+    // taken, so the warps of the block finish together although their
+    // queries' costs differ (the block's slot on the SM is free only when its
+    // last warp is done).
+    for (int32_t t0 = threadIdx.x & ~31; t0 < total;) {
         const int32_t t = t0 + (threadIdx.x & 31);
         const bool active = t < total;
         int32_t qp = 0;
@@ -456,6 +462,9 @@ __device__ __forceinline__ void rim_sector(const Plan &p, const QueryBufs &b, in
             qp = s_beg[j] + (t - s_pre[j]);
         }
         thread_query<F64, false>(p, b, qp, active, nullptr, nullptr, n_cand, n_re, n_edge);
+        int32_t nx = 0;
+        if ((threadIdx.x & 31) == 0) nx = atomicAdd(&s_next, 32);
+        t0 = __shfl_sync(0xffffffffu, nx, 0);
     }
     add_stats(b.stats, n_cand, n_re, n_edge);
 }
@@ -596,10 +605,11 @@ __device__ __forceinline__ int graph_search(const int64_t *__restrict__ off, int
 }
 
 // Count pass.  One graph: block x is sector x.  A batch: block x is global
-// sector x; the sector table gives its graph.  Four CTAs per SM leave 64
-// registers a thread, room for the candidate prefetch without spilling.
+// sector x; the sector table gives its graph.  Eight blocks of four warps per
+// SM leave 64 registers a thread, room for the candidate prefetch; small
+// blocks free their SM slot soon after their sector's last query.
 template <bool F64, bool BATCH>
-__global__ void __launch_bounds__(kRimThreads, 4) k_rim_sector(Plan p, QueryBufs b)
+__global__ void __launch_bounds__(kRimThreads, 8) k_rim_sector(Plan p, QueryBufs b)
 {
     if (BATCH) {
         const int g = graph_search(b.sec_off, b.NG, blockIdx.x);
