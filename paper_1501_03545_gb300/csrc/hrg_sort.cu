@@ -27,6 +27,7 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kWarps = kSortThreads / 32;
+constexpr int kSortRowsPerBlock = 16 * kWarps;
 constexpr int kCtaThreads = 512;  // CTA bucket sort
 constexpr int kCtaWarps = kCtaThreads / 32;
 constexpr int kSetupThreads = 1024;  // k_big_setup needs whole warps (shuffle scans)
@@ -127,17 +128,11 @@ __device__ __forceinline__ void warp_sort_regs(int32_t *row, int d, int lane)
         if (lane + 32 * r < d) row[lane + 32 * r] = v[r];
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ cnt,
-                                                            int64_t n, const int32_t *__restrict__ graph_of,
-                                                            const int64_t *__restrict__ noff,
-                                                            const int64_t *__restrict__ row_off, int32_t *col_idx)
+// One row of the warp sort (33..kWarpRow ids).
+__device__ __forceinline__ void warp_sort_row(WarpSortSmem &S, int32_t id, int64_t n,
+                                              const int32_t *__restrict__ graph_of, const int64_t *__restrict__ noff,
+                                              const int64_t *__restrict__ row_off, int32_t *col_idx, int lane)
 {
-    __shared__ WarpSortSmem sm[kWarps];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * kWarps + w;
-    if (r >= *cnt) return;
-    WarpSortSmem &S = sm[w];
-    const int32_t id = rows[r];
     const int64_t base = row_off[id];
     const int d = (int)(row_off[id + 1] - base);
     int32_t *row = col_idx + base;
@@ -180,6 +175,29 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__res
     sort_buckets(S.key, S.cnt, nb, 0, 32, lane);
     __syncwarp();
     for (int i = lane; i < d; i += 32) row[i] = (int32_t)S.key[i];
+}
+
+// kSortRowsPerBlock rows a block: warp w sorts row w first, then the next row
+// not yet taken (a shared counter), so the block's warps end together
+// although the rows' lengths differ.
+__global__ void __launch_bounds__(kSortThreads) k_sort_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ cnt,
+                                                            int64_t n, const int32_t *__restrict__ graph_of,
+                                                            const int64_t *__restrict__ noff,
+                                                            const int64_t *__restrict__ row_off, int32_t *col_idx)
+{
+    __shared__ WarpSortSmem sm[kWarps];
+    __shared__ int32_t s_next;
+    if (threadIdx.x == 0) s_next = kWarps;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * kSortRowsPerBlock, nr = *cnt;
+    for (int k = w; k < kSortRowsPerBlock && r0 + k < nr;) {
+        warp_sort_row(sm[w], rows[r0 + k], n, graph_of, noff, row_off, col_idx, lane);
+        __syncwarp();
+        int32_t nx = 0;
+        if (lane == 0) nx = atomicAdd(&s_next, 1);
+        k = __shfl_sync(0xffffffffu, nx, 0);
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -575,7 +593,7 @@ cudaError_t launch_sort_rows(const Plan &p, const QueryBufs &b, const int32_t co
         attr = true;
     }
     if (counts[0] > 0)
-        k_sort_warp<<<(unsigned)((counts[0] + kWarps - 1) / kWarps), kSortThreads, 0, s>>>(
+        k_sort_warp<<<(unsigned)((counts[0] + kSortRowsPerBlock - 1) / kSortRowsPerBlock), kSortThreads, 0, s>>>(
             b.rows[0], b.list_cnt + 0, p.n, b.graph_of, b.noff, row_off, col_idx);
     if (counts[1] > 0)
         k_sort_cta_rows<<<(unsigned)counts[1], kCtaThreads, sizeof(SortSmem), s>>>(
