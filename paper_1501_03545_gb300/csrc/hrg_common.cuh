@@ -76,51 +76,68 @@ __device__ __forceinline__ U4 philox_block(uint64_t ctr, uint64_t seed)
     return s;
 }
 
-// Natural logarithm of a normal double x >= 1 by the table-driven reduction
-// of P. T. P. Tang (ACM TOMS 16(4), 1990): x = 2^e (F_j + f) with
-// F_j = 1 + j/128 (j = the top 7 mantissa bits) and 0 <= f < 1/128, so
-//   log x = e ln 2 + log F_j + log(1 + t),  t = f / F_j in [0, 2^-7),
-// with log(1 + t) from its Taylor series through t^6/6 (the next term is
-// below 2^-51.8, under 0.1 ulp of any result >= 16).  tab[j] = 1 / F_j and
-// tab[128 + j] = log F_j are tabulated on the host.  ln 2 is split into a
-// 40-bit head (e times it is exact) and the rounded remainder.
-constexpr double kLn2Hi = 0x1.62e42fefa4p-1;
-constexpr double kLn2Lo = -0x1.8432a1b0e2634p-43;
-
-__device__ __forceinline__ double log_table(double x, const double *tab)
-{
-    const long long bits = __double_as_longlong(x);
-    const int e = (int)(bits >> 52) - 1023;
-    const int j = (int)((bits >> 45) & 127);
-    const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
-    const double F = __longlong_as_double(0x3FF0000000000000ll | ((long long)j << 45));
-    const double t = (m - F) * tab[j];  // m - F is exact
-    double c = -1.0 / 6.0;
-    c = fma(c, t, 1.0 / 5.0);
-    c = fma(c, t, -1.0 / 4.0);
-    c = fma(c, t, 1.0 / 3.0);
-    c = fma(c, t, -1.0 / 2.0);
-    const double l1p = fma(c * t, t, t);
-    return fma((double)e, kLn2Hi, tab[128 + j]) + fma((double)e, kLn2Lo, l1p);
-}
-
-// acosh(x) for x >= 2^8 from the series
+// acosh(x) for a double x >= 2^8, in unsigned 64-bit fixed point (integer
+// multiplies instead of the FP64 pipe), from
 //   acosh(x) = log(2x) + log((1 + sqrt(1 - s)) / 2)
-//            = log(2x) - s/4 - 3 s^2/32 - 5 s^3/96 - 35 s^4/1024 - ...,  s = 1/x^2.
-// With s <= 2^-16 the first dropped term is below 2^-68; for x >= 2^24 the
-// whole sum is below 2^-50 against log(2x) > 17 and is skipped.  s comes from
-// the float reciprocal of x refined by one Newton step (relative error
-// ~2^-46, i.e. ~2^-64 absolute in s/4).
-__device__ __forceinline__ double acosh_series(double x, const double *log_tab)
+//            = log(2x) - s/4 - 3 s^2/32 - 5 s^3/96 - ...,  s = 1/x^2 <= 2^-16
+// (the first dropped term, 35 s^4/1024, is below 2^-69).
+// log(2x) by the table-driven reduction of P. T. P. Tang (ACM TOMS 16(4),
+// 1990): 2x = 2^e (F_j + f) with F_j = 1 + j/128 (j = the top 7 mantissa
+// bits) and 0 <= f < 1/128, so
+//   log 2x = e ln 2 + log F_j + log(1 + t),  t = f / F_j in [0, 2^-7).
+// tab[j] = floor(2^63 / F_j), tab[128 + j] = log F_j 2^64 and tab[256] =
+// ln 2 2^64, rounded, are computed on the host in integer arithmetic.
+// t is formed as T = t 2^70 (truncations below 2^-70); log(1 + t) = t h_1
+// with h_8 = 1/8, h_k = 1/k - t h_{k+1} in Q63 (the dropped term t^9/9 is
+// below 2^-66; each step truncates below 2^-63, weighed by t <= 2^-7).
+// s from the same reduction: x = 2^(e-1) m, 1/m = (1/F_j) / (1 + t) with
+// 1/(1 + t) by its series through t^7 in Q63 (dropped: t^8 < 2^-56,
+// relative), so s is within ~2^-55 relative and the correction within
+// ~2^-64.  The sum is kept with 64 fraction bits and rounded to the nearest
+// double once: within 0.5 ulp + ~2^-60 of acosh(x).
+__device__ __forceinline__ double acosh_fix(double x, const uint64_t *tab)
 {
-    double a = log_table(x + x, log_tab);
-    if (x < 0x1p24) {
-        const double y0 = (double)__frcp_rn((float)x);
-        const double y = fma(y0, fma(-x, y0, 1.0), y0);
-        const double s = y * y;
-        a -= s * fma(s, fma(s, 5.0 / 96.0, 3.0 / 32.0), 0.25);
+    const uint64_t bits = (uint64_t)__double_as_longlong(x);
+    const uint64_t e = (bits >> 52) - 1022;  // exponent of 2x, >= 9
+    const int j = (int)((bits >> 45) & 127);
+    const uint64_t f45 = bits & ((1ull << 45) - 1);
+    // T = f45 2^-52 (tab[j] 2^-63) 2^70 = (f45 tab[j]) >> 45
+    const uint64_t inv = tab[j];
+    const uint64_t T = (__umul64hi(f45, inv) << 19) | ((f45 * inv) >> 45);
+    uint64_t h = (1ull << 63) / 8, g = 1ull << 63;
+#pragma unroll
+    for (int k = 7; k >= 1; --k) {
+        h = ((1ull << 63) / k) - (__umul64hi(T, h) >> 6);  // (t h) 2^63 = (T h) >> 70
+        if (k <= 6) g = (1ull << 63) - (__umul64hi(T, g) >> 6);
     }
-    return a;
+    g = (1ull << 63) - (__umul64hi(T, g) >> 6);  // g_0
+    const uint64_t L = __umul64hi(T, h) >> 5;    // t h_1 2^64 = (T h_1) >> 69
+    // (1/m)^2, ^4, ^6 in Q63; s = (1/m)^2 2^(2 - 2e)
+    const uint64_t rm = __umul64hi(inv, g) << 1;
+    const uint64_t q2 = __umul64hi(rm, rm) << 1, q4 = __umul64hi(q2, q2) << 1, q6 = __umul64hi(q4, q2) << 1;
+    // the correction times 2^64 (x = 2^(e-1) m): s/4 = q2 >> (2e - 1),
+    // 3 s^2/32 = 3 q4 >> 4e, 5 s^3/96 = 5 q6 / 96 >> (6e - 7)
+    const unsigned s1 = (unsigned)(2 * e - 1), s2 = (unsigned)(4 * e - 2), s3 = (unsigned)(6 * e - 7);
+    uint64_t corr = s1 < 64 ? q2 >> s1 : 0;
+    if (s2 < 64) corr += (3 * (q4 >> 2)) >> s2;
+    if (s3 < 64) corr += ((q6 / 96) * 5) >> s3;
+    // e ln 2 + log F_j + L - corr as hi + lo 2^-64
+    uint64_t lo = e * tab[256], hi = __umul64hi(e, tab[256]);
+    const uint64_t a = lo + tab[128 + j];
+    hi += a < lo;
+    lo = a + L;
+    hi += lo < a;
+    hi -= lo < corr;
+    lo -= corr;
+    // round hi + lo 2^-64 (hi >= 6) to 53 bits, to nearest, ties to even
+    const int nb = 64 - __clzll((long long)hi);  // integer bits
+    const int sh = nb + 11;                      // bits dropped, 14..21
+    uint64_t m = (hi << (64 - sh)) | (lo >> sh);
+    const uint64_t rem = lo & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    m += (rem > half || (rem == half && (m & 1))) ? 1 : 0;
+    // m carries the leading bit at 2^52 (2^53 after a carry, which then
+    // raises the exponent): value m 2^(nb - 53)
+    return __longlong_as_double((long long)(((uint64_t)(nb - 2 + 1023) << 52) + m));
 }
 
 // The uniform of a 64-bit word is u = k 2^-53, k its top 53 bits.  Its
@@ -139,10 +156,10 @@ __device__ __forceinline__ double top53(uint32_t hi, uint32_t lo)
 // 2^-53.  Above x = 2^8 the series (no square root, and one short branch
 // where the library acosh would make a warp run both paths); below, the
 // library acosh.
-__device__ __forceinline__ double radius_of(double k_r, double big_scaled, double inv_alpha, const double *log_tab)
+__device__ __forceinline__ double radius_of(double k_r, double big_scaled, double inv_alpha, const uint64_t *log_tab)
 {
     const double x = __dadd_rn(1.0, __dmul_rn(k_r, big_scaled));
-    const double a = x >= 0x1p8 ? acosh_series(x, log_tab) : acosh(x);
+    const double a = x >= 0x1p8 ? acosh_fix(x, log_tab) : acosh(x);
     return a * inv_alpha;
 }
 

@@ -19,12 +19,14 @@ constexpr int kThreads = 256;
 constexpr int kSampleGrid = 152 * 16;  // persistent grid of the samplers (each CTA loads the log table once)
 constexpr int kSplitGrid = 152 * 8;    // persistent: the split reads the records front to back
 
-// 1/F_j and log F_j, F_j = 1 + j/128 (log_table); filled once per device
-__device__ double g_log_tab[256];
+// 2^63 / F_j, log F_j 2^64 (F_j = 1 + j/128) and ln 2 2^64 (log_fix); filled
+// once per device
+constexpr int kLogTab = 257;
+__device__ uint64_t g_log_tab[kLogTab];
 
-__device__ __forceinline__ void load_log_tab(double *s_tab)
+__device__ __forceinline__ void load_log_tab(uint64_t *s_tab)
 {
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) s_tab[k] = g_log_tab[k];
+    for (int k = threadIdx.x; k < kLogTab; k += blockDim.x) s_tab[k] = g_log_tab[k];
     __syncthreads();
 }
 
@@ -56,7 +58,7 @@ __global__ void k_sample_bucket(Plan p, uint64_t seed, double *__restrict__ r_ou
                                 int32_t *__restrict__ gbuf, int32_t *__restrict__ slot, int32_t *__restrict__ cnt,
                                 int64_t *__restrict__ band_cnt)
 {
-    __shared__ double s_tab[256];
+    __shared__ uint64_t s_tab[kLogTab];
     __shared__ int sh[HRG_MAX_BANDS];
     for (int k = threadIdx.x; k < HRG_MAX_BANDS; k += blockDim.x) sh[k] = 0;
     load_log_tab(s_tab);
@@ -173,7 +175,7 @@ __global__ void k_sample_bucket_batch(const Plan *__restrict__ plans, const int3
                                       int32_t *__restrict__ gbuf, int32_t *__restrict__ slot,
                                       int32_t *__restrict__ cnt)
 {
-    __shared__ double s_tab[256];
+    __shared__ uint64_t s_tab[kLogTab];
     load_log_tab(s_tab);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
@@ -404,14 +406,46 @@ cudaError_t launch_scatter_soa(const Plan &p, const int32_t *gbuf, const int32_t
     return cudaGetLastError();
 }
 
+namespace {
+
+typedef unsigned __int128 u128;
+
+// floor(a b / 2^127) for a, b < 2^127 (numbers below 1 in Q127), from 64-bit
+// limbs: exact integer arithmetic, the same on every host
+u128 mul_q127(u128 a, u128 b)
+{
+    const uint64_t a0 = (uint64_t)a, a1 = (uint64_t)(a >> 64), b0 = (uint64_t)b, b1 = (uint64_t)(b >> 64);
+    const u128 t0 = (u128)a0 * b0, t1 = (u128)a1 * b0, t2 = (u128)a0 * b1, t3 = (u128)a1 * b1;
+    const u128 mid = (t0 >> 64) + (uint64_t)t1 + (uint64_t)t2;
+    const u128 hi = t3 + (t1 >> 64) + (t2 >> 64) + (mid >> 64);
+    return (hi << 1) | ((uint64_t)mid >> 63);
+}
+
+// log(num / den) 2^64, rounded, for 1 <= num / den <= 2: 2 atanh(u) with
+// u = (num - den) / (num + den) <= 1/3 by its series u + u^3/3 + ... in
+// Q127 (each step truncates below 2^-126; the terms fall by u^2 <= 1/9)
+uint64_t log_ratio_q64(unsigned num, unsigned den)
+{
+    const u128 u = (((u128)(num - den) << 120) / (num + den)) << 7;
+    const u128 u2 = mul_q127(u, u);
+    u128 sum = 0, term = u;
+    for (unsigned k = 1; term != 0; k += 2) {
+        sum += term / k;
+        term = mul_q127(term, u2);
+    }
+    return (uint64_t)((sum + ((u128)1 << 61)) >> 62);  // 2 sum 2^64 / 2^127, rounded
+}
+
+}  // namespace
+
 cudaError_t upload_log_table()
 {
-    double tab[256];
-    for (int j = 0; j < 128; ++j) {
-        const double F = 1.0 + j / 128.0;
-        tab[j] = 1.0 / F;
-        tab[128 + j] = std::log(F);
+    uint64_t tab[kLogTab];
+    for (unsigned j = 0; j < 128; ++j) {
+        tab[j] = (uint64_t)(((u128)1 << 70) / (128 + j));  // floor(2^63 / F_j), F_j = (128 + j) / 128
+        tab[128 + j] = log_ratio_q64(128 + j, 128);
     }
+    tab[256] = log_ratio_q64(2, 1);
     return cudaMemcpyToSymbol(g_log_tab, tab, sizeof tab);
 }
 

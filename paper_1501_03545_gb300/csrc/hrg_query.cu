@@ -966,7 +966,7 @@ __global__ void k_hub_check_pooled(QueryBufs b, int32_t p_hub)
         atomicOr((unsigned long long *)&b.stats[ST_ERR], 1ull);
 }
 
-constexpr unsigned kHeavyGrid = 152 * 8;
+constexpr unsigned kHeavyGrid = 152 * 16;
 
 template <bool F64, bool WRITE, bool BATCH>
 static void hub_launch(const Plan &p, const QueryBufs &b, int32_t p_hub, const int64_t *row_off, cudaStream_t s)
