@@ -153,9 +153,9 @@ __device__ __forceinline__ double top53(uint32_t hi, uint32_t lo)
 
 // Radius of Eq. (1)'s inverse CDF, r = acosh(x) / alpha with x = 1 + u_r
 // (cosh(alpha R) - 1) = 1 + k_r big_scaled, big_scaled = (cosh(alpha R) - 1)
-// 2^-53.  Above x = 2^8 the series (no square root, and one short branch
-// where the library acosh would make a warp run both paths); below, the
-// library acosh.
+// 2^-53.  Above x = 2^8 the fixed-point series (acosh_fix: integer pipes,
+// one short branch where the library acosh would make a warp run both
+// paths); below, the library acosh.
 __device__ __forceinline__ double radius_of(double k_r, double big_scaled, double inv_alpha, const uint64_t *log_tab)
 {
     const double x = __dadd_rn(1.0, __dmul_rn(k_r, big_scaled));

@@ -7,7 +7,8 @@
 namespace hrg {
 
 // ---- points (hrg_points.cu) ----
-// The sampler's table of 1/F_j and log F_j (log_table); once per device.
+// The sampler's table of 2^63 / F_j, log F_j 2^64 and ln 2 2^64 (acosh_fix);
+// once per device.
 cudaError_t upload_log_table();
 // Sampler of Algorithm 1 (angle and radius draws, Eq. (1)): writes r, phi in
 // vertex-id order, and with them every point's angular bucket (gbuf), its
