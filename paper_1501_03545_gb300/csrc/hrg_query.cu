@@ -634,6 +634,7 @@ __global__ void __launch_bounds__(kRimThreads, 8) k_rim_sector(Plan p, QueryBufs
 // overflowed does it traverse them again.
 // ---------------------------------------------------------------------------
 constexpr int kHubStage = 1024;
+constexpr int kHubPer = 2;  // candidates a lane per step of a hub query's walk
 constexpr int kPoolRunShift = 40;  // pool_cur[0] = runs << 40 | entries: one atomic reserves both
 
 // a run of `fill` ids: (pool offset, run index), or false when the pool or
@@ -716,32 +717,50 @@ __device__ __forceinline__ void hub_query(const Plan &p, const QueryBufs &b, int
                 }
                 continue;
             }
-            for (int32_t c0 = s; c0 < e; c0 += 64) {
-                const int32_t ca = c0 + lane, cb = c0 + 32 + lane;
-                const bool va = ca < e && ca != qp, vb = cb < e && cb != qp;
-                uint64_t Aa = 0, Ab = 0;
-                PMS pa{}, pb{};
-                if (va) { Aa = __ldg(b.A + ca); pa = b.pms[ca]; }
-                if (vb) { Ab = __ldg(b.A + cb); pb = b.pms[cb]; }
-                const bool ea = va && decide_loaded<F64>(p, b, q, q64, Aq, Aa, pa, ca, rg.W, n_cand, n_re);
-                const bool eb = vb && decide_loaded<F64>(p, b, q, q64, Aq, Ab, pb, cb, rg.W, n_cand, n_re);
+            // kHubPer candidates a lane per step, their loads in flight together
+            for (int32_t c0 = s; c0 < e; c0 += 32 * kHubPer) {
+                bool v[kHubPer], ed[kHubPer];
+                uint64_t Ac[kHubPer];
+                PMS pc[kHubPer];
+#pragma unroll
+                for (int u = 0; u < kHubPer; ++u) {
+                    const int32_t c = c0 + 32 * u + lane;
+                    v[u] = c < e && c != qp;
+                    Ac[u] = 0;
+                    pc[u] = PMS{};
+                    if (v[u]) {
+                        Ac[u] = __ldg(b.A + c);
+                        pc[u] = b.pms[c];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kHubPer; ++u)
+                    ed[u] = v[u] && decide_loaded<F64>(p, b, q, q64, Aq, Ac[u], pc[u], c0 + 32 * u + lane, rg.W,
+                                                       n_cand, n_re);
                 if (WRITE) {
-                    warp_put(b.col_out, base, lim, pos, ea, pa.id - p.id_off, lt);
-                    warp_put(b.col_out, base, lim, pos, eb, pb.id - p.id_off, lt);
+#pragma unroll
+                    for (int u = 0; u < kHubPer; ++u) warp_put(b.col_out, base, lim, pos, ed[u], pc[u].id - p.id_off, lt);
                 } else {
-                    mine += (int)ea + (int)eb;
+                    unsigned m[kHubPer];
+                    int32_t add = 0;
+#pragma unroll
+                    for (int u = 0; u < kHubPer; ++u) {
+                        mine += (int)ed[u];
+                        m[u] = __ballot_sync(0xffffffffu, ed[u]);
+                        add += __popc(m[u]);
+                    }
                     if (pooled) {
-                        const unsigned ma = __ballot_sync(0xffffffffu, ea), mb = __ballot_sync(0xffffffffu, eb);
-                        const int32_t add = __popc(ma) + __popc(mb);
                         if (fill + add > kHubStage) {
                             __syncwarp();
                             pool_flush(b, qi, stage, fill, lane);
                             __syncwarp();
                             fill = 0;
                         }
-                        if (ea) stage[fill + __popc(ma & lt)] = pa.id - p.id_off;
-                        if (eb) stage[fill + __popc(ma) + __popc(mb & lt)] = pb.id - p.id_off;
-                        fill += add;
+#pragma unroll
+                        for (int u = 0; u < kHubPer; ++u) {
+                            if (ed[u]) stage[fill + __popc(m[u] & lt)] = pc[u].id - p.id_off;
+                            fill += __popc(m[u]);
+                        }
                     }
                 }
             }
