@@ -165,7 +165,7 @@ struct QueryBufs {
     int64_t n_sectors;        // rim sectors over all graphs
 };
 
-constexpr int kHeavy = 4096;      // hub ranges longer than this are split into chunks for whole CTAs
+constexpr int kHeavy = 8192;      // hub ranges longer than this are split into chunks for whole CTAs
 
 // Degrees of hub-band vertices (one warp each, long ranges as CTA chunks).
 // deg must be zero for them beforehand.
