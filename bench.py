@@ -233,7 +233,7 @@ def run_serving(H, device, seconds, slots, rate=W.SERVE_RATE):
         big = max(reqs, key=lambda q: q[1])
         warm = [srv.submit(big[1], big[2], big[3], big[4]) for _ in range(2 * slots)]
         for t in warm:
-            srv.wait(t)
+            srv.wait(t, timeout_s=300.0)
             srv.release(t)
         base = srv.counters()
         todo = queue.Queue()
@@ -245,7 +245,7 @@ def run_serving(H, device, seconds, slots, rate=W.SERVE_RATE):
                 t = todo.get()
                 if t is None:
                     return
-                res = srv.wait(t)
+                res = srv.wait(t, timeout_s=300.0)
                 with lock:
                     done.append((res.status, res.submit_s, res.done_s, res.n_entries, res.batch_size))
                 srv.release(t)

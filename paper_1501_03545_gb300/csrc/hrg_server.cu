@@ -266,7 +266,10 @@ void worker_main(hrg_server *s, int slot)
                 ++s->running;
                 if (s->running > s->max_running) s->max_running = s->running;
             }
-            if (!s->queue.empty()) s->cv_work.notify_one();
+            // every worker: whether the next request fits depends on the worker
+            // (its resident workspace), so a single wake-up could reach one that
+            // cannot take it and leave the one that can asleep
+            if (!s->queue.empty()) s->cv_work.notify_all();
         }
         if (batch.empty()) continue;
         if (!ok) {
@@ -341,7 +344,7 @@ extern "C" int hrg_server_submit(hrg_server *s, const hrg_params *p, int64_t *ti
     *ticket = q->ticket;
     s->queue.push_back(q.get());
     s->reqs.emplace(q->ticket, std::move(q));
-    s->cv_work.notify_one();
+    s->cv_work.notify_all();  // all workers: only some may be able to take it
     return HRG_OK;
 }
 

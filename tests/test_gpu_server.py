@@ -7,6 +7,10 @@ from paper_1501_03545_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
+# a bound on every wait, so that a request that never runs fails the test
+# instead of holding it
+WAIT_S = 300.0
+
 
 @pytest.fixture(scope="module")
 def H():
@@ -32,7 +36,7 @@ def test_mix_equals_alone(H):
         tickets = [srv.submit(n, a, k, s) for (_, n, a, k, s) in reqs]
         sizes = []
         for t, (_, n, a, k, s) in zip(tickets, reqs):
-            res = srv.wait(t)
+            res = srv.wait(t, timeout_s=WAIT_S)
             assert res.status == H.HRG_OK, srv.last_error()
             assert res.n == n
             sizes.append(res.batch_size)
@@ -62,7 +66,7 @@ def test_memory_admission(H):
         assert e.value.code == H.HRG_ENOMEM
         tickets = [srv.submit(n, 0.8, kbar, 100 + k) for k in range(8)]
         for t in tickets:
-            res = srv.wait(t)
+            res = srv.wait(t, timeout_s=WAIT_S)
             assert res.status == H.HRG_OK
             assert res.batch_size <= 2
             srv.release(t)
@@ -83,7 +87,7 @@ def test_unknown_ticket_and_timeout(H):
             srv.wait(t, timeout_s=0.0)
         except TimeoutError:
             pass  # still running: the limit was respected
-        res = srv.wait(t)
+        res = srv.wait(t, timeout_s=WAIT_S)
         assert res.status == H.HRG_OK and res.n_entries > 0
         srv.release(t)
     finally:
@@ -100,7 +104,7 @@ def test_served_graphs_equal_the_oracle(H):
     try:
         tickets = [srv.submit(n, a, k, sd) for (n, a, k, sd) in reqs]
         for t, (n, a, k, sd) in zip(tickets, reqs):
-            res = srv.wait(t)
+            res = srv.wait(t, timeout_s=WAIT_S)
             assert res.status == H.HRG_OK
             r, phi, off, col = srv.fetch(res)
             R = O.solve_radius(n, a, k)
@@ -128,7 +132,7 @@ def test_admission_counts_resident_workspace(H):
     srv = H.Server(0, slots=2)
     try:
         big = srv.submit(6_000_000, 0.6, 16.0, 5)
-        res = srv.wait(big)
+        res = srv.wait(big, timeout_s=WAIT_S)
         assert res.status == H.HRG_OK
         torch.cuda.synchronize()
         free1, _ = torch.cuda.mem_get_info()
@@ -139,7 +143,7 @@ def test_admission_counts_resident_workspace(H):
         srv.release(big)
         small = [srv.submit(50_000 + 1000 * k, 0.8, 8.0, 20 + k) for k in range(6)]
         for t in small:
-            assert srv.wait(t).status == H.HRG_OK
+            assert srv.wait(t, timeout_s=WAIT_S).status == H.HRG_OK
             srv.release(t)
         c = srv.counters()
         assert c["in_use_bytes"] == c["resident_bytes"] and c["peak_in_use_bytes"] <= c["budget_bytes"]
@@ -152,7 +156,7 @@ def test_admission_counts_resident_workspace(H):
     try:
         for k in range(4):
             t = srv.submit(n, 0.6, 16.0, 40 + k)
-            assert srv.wait(t).status == H.HRG_OK
+            assert srv.wait(t, timeout_s=WAIT_S).status == H.HRG_OK
             srv.release(t)
         c = srv.counters()
         assert c["completed"] == 4 and c["peak_in_use_bytes"] <= c["budget_bytes"]
