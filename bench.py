@@ -595,8 +595,8 @@ def main():
                 "ms": stage["count"] + stage["offsets"] + stage["write"] + stage["rowsort"]}}
     qc = roof["query_csr_roofline"]
     qc["frac"] = qc["bytes"] / (qc["ms"] / 1e3) / 1e9 / peak
-    # the roof that binds this kernel: instruction issue (see DESIGN: 60 % of
-    # issue slots used, 8 % of DRAM throughput)
+    # its instruction-issue rate against the issue roof (the pass is far from
+    # the HBM roof: a few per cent of DRAM throughput)
     inst = NCU_INSTRUCTIONS.get(source_hash()) if w.n == WORKLOAD.n else None
     roof["issue_roof"] = None if inst is None else {
         "warp_instructions": inst, "achieved": inst / (stage["count_rim"] / 1e3), "peak": ISSUE_PEAK,
