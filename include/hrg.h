@@ -266,6 +266,12 @@ int hrg_generate_finish(hrg_job *job, int32_t *col_idx_out);
  *   heavy_segments  first capacity of the list of long hub ranges (automatic:
  *                   max(2^16, n/64)); when it overflows the count pass runs
  *                   once more with room for all (heavy_retries)
+ *   workspace_bytes the most device memory the context's workspace may hold
+ *                   (0: no cap); a call that would need more returns
+ *                   HRG_ENOMEM, as when the device itself has no room, and
+ *                   the context stays usable (a smaller graph, a higher cap
+ *                   or hrg_release_workspace, which gives back what the
+ *                   context holds, lets the next call run)
  * Errors: HRG_EINVAL (negative or oversized value), HRG_ESTATE (a job is open).
  */
 typedef struct hrg_limits {
@@ -273,6 +279,7 @@ typedef struct hrg_limits {
     int64_t hub_pool_ids;
     int32_t hub_runs;
     int32_t heavy_segments;
+    int64_t workspace_bytes;
 } hrg_limits;
 
 int hrg_set_limits(hrg_ctx *ctx, const hrg_limits *lim);

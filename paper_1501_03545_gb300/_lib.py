@@ -60,7 +60,7 @@ class hrg_stats(ctypes.Structure):
 
 class hrg_limits(ctypes.Structure):
     _fields_ = [("row_buffer_ids", ctypes.c_int64), ("hub_pool_ids", ctypes.c_int64), ("hub_runs", ctypes.c_int32),
-                ("heavy_segments", ctypes.c_int32)]
+                ("heavy_segments", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64)]
 
 
 class hrg_props(ctypes.Structure):
@@ -211,10 +211,11 @@ class Context:
         """hrg_release_workspace: free the context's workspace."""
         self.check(load().hrg_release_workspace(self.h))
 
-    def set_limits(self, row_buffer_ids=0, hub_pool_ids=0, hub_runs=0, heavy_segments=0):
+    def set_limits(self, row_buffer_ids=0, hub_pool_ids=0, hub_runs=0, heavy_segments=0, workspace_bytes=0):
         """hrg_set_limits: capacities of the count pass's buffers for later
-        jobs (0: automatic)."""
-        lim = hrg_limits(int(row_buffer_ids), int(hub_pool_ids), int(hub_runs), int(heavy_segments))
+        jobs (0: automatic) and a cap on the context's workspace (0: none)."""
+        lim = hrg_limits(int(row_buffer_ids), int(hub_pool_ids), int(hub_runs), int(heavy_segments),
+                         int(workspace_bytes))
         self.check(load().hrg_set_limits(self.h, ctypes.byref(lim)))
 
 

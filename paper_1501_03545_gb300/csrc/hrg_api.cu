@@ -1,6 +1,7 @@
 // hrg_api.cu -- the C ABI (include/hrg.h): contexts, jobs, workspace, plan.
 #include <algorithm>
 #include <cmath>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -135,6 +136,7 @@ struct hrg_ctx {
     DevBuf ws[W_COUNT];
     void *pinned = nullptr;  // small pinned staging area for read-backs
     cudaEvent_t ev[10] = {};  // stage boundaries of the current job
+    bool nvtx_open = false;   // a stage's NVTX range is open on the host thread (stage_mark)
     cudaStream_t work = nullptr, copy = nullptr;  // hrg_generate_host: generation and read-back streams
     // hrg_generate_host: [0] points sampled, [1] [2] first and last read-back
     // on the copy stream, then four per range of the chunked write pass
@@ -167,6 +169,20 @@ static int set_err(hrg_ctx *c, int code, const char *fmt, ...)
 // Kept-row buffer of the rim count pass: room for 32 entries per vertex.  The
 // scatter's 32-byte point records use it before the count pass.
 static int64_t small_capacity(int64_t n) { return std::min<int64_t>(32 * n + 1024, 0x7fff0000LL); }
+// Stage boundary k of a job: the CUDA event that times the stages, and an
+// NVTX range on the host thread around the launches of the stage that starts
+// there (for profilers that record NVTX; a no-op otherwise).
+static cudaError_t stage_mark(hrg_ctx *ctx, int k, cudaStream_t st)
+{
+    static const char *const names[10] = {"hrg sample",    "hrg bands", "hrg count hub", "hrg count rim",
+                                          "hrg offsets",   nullptr,     "hrg write",     "hrg write rim",
+                                          "hrg row sort",  nullptr};
+    if (ctx->nvtx_open) nvtxRangePop();
+    ctx->nvtx_open = names[k] != nullptr;
+    if (ctx->nvtx_open) nvtxRangePushA(names[k]);
+    return cudaEventRecord(ctx->ev[k], st);
+}
+
 static size_t small_bytes(int64_t n)
 {
     return std::max(sizeof(int32_t) * (size_t)small_capacity(n), sizeof(PointRec) * (size_t)n);
@@ -180,7 +196,16 @@ static int ensure(hrg_ctx *ctx, int slot, size_t bytes, void **out)
         if (b.ptr) cudaFree(b.ptr);
         b.ptr = nullptr;
         b.bytes = 0;
-        const size_t want = bytes + bytes / 8;  // grow with some slack
+        size_t want = bytes + bytes / 8;  // grow with some slack
+        if (ctx->lim.workspace_bytes > 0) {  // the caller's cap on the whole workspace
+            size_t held = 0;
+            for (const auto &o : ctx->ws) held += o.bytes;
+            const size_t cap = (size_t)ctx->lim.workspace_bytes;
+            if (held + bytes > cap)
+                return set_err(ctx, HRG_ENOMEM, "workspace of %zu bytes would exceed its cap of %zu", held + bytes,
+                               cap);
+            if (held + want > cap) want = bytes;
+        }
         cudaError_t e = cudaMalloc(&b.ptr, want);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -277,7 +302,7 @@ extern "C" int hrg_set_limits(hrg_ctx *ctx, const hrg_limits *lim)
     hrg_limits l{};
     if (lim) l = *lim;
     if (l.row_buffer_ids < 0 || l.hub_pool_ids < 0 || l.hub_pool_ids >= (1LL << 40) || l.hub_runs < 0 ||
-        l.hub_runs >= (1 << 24) || l.heavy_segments < 0)
+        l.hub_runs >= (1 << 24) || l.heavy_segments < 0 || l.workspace_bytes < 0)
         return set_err(ctx, HRG_EINVAL, "limits out of range");
     ctx->lim = l;
     return HRG_OK;
@@ -475,14 +500,14 @@ static int count_and_offsets(hrg_ctx *ctx, hrg_job &J, int64_t n, cudaStream_t s
         CK(cudaMemsetAsync(small_cur, 0, sizeof(unsigned long long), st));
         CK(cudaMemsetAsync(small_off, 0xFF, sizeof(int32_t) * n, st));  // -1: no kept row (hub positions too)
         CK(launch_count_hub(p, b, J.fp64, J.p_hub, st));
-        CK(cudaEventRecord(ctx->ev[3], st));
+        CK(stage_mark(ctx, 3, st));
         CK(launch_count_rim(p, b, J.fp64, st));
-        CK(cudaEventRecord(ctx->ev[4], st));
+        CK(stage_mark(ctx, 4, st));
 
         // 4. row offsets; the totals, the list lengths (the heavy hub
         // segments among them) and the counters come back together
         CK(scan_i32_to_i64((int32_t *)deg, row_off_out, n, scanws, st));
-        CK(cudaEventRecord(ctx->ev[5], st));
+        CK(stage_mark(ctx, 5, st));
         CK(cudaMemcpyAsync(hp + 0, row_off_out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(hp + 8, listcnt, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(hp + 24, bigtot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -578,7 +603,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
         if ((e = ensure(ctx, hrg_ctx::W_SCAN, scan_bytes, &scanws))) return e;
         return HRG_OK;
     };
-    CK(cudaEventRecord(ctx->ev[0], st));
+    CK(stage_mark(ctx, 0, st));
     CK(cudaMemsetAsync(band_cnt, 0, sizeof(int64_t) * HRG_MAX_BANDS, st));
     if (sampled) {
         expected_band_counts(p, cnt_copy);
@@ -588,7 +613,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
                                 (int64_t *)band_cnt, st));
         J.r = r_out;
         J.phi = phi_out;
-        CK(cudaEventRecord(ctx->ev[1], st));
+        CK(stage_mark(ctx, 1, st));
         if (hpts) {
             CK(cudaEventRecord(hpts->sampled, st));
             CK(cudaStreamWaitEvent(hpts->copy, hpts->sampled, 0));
@@ -604,7 +629,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
         CK(cudaMemcpyAsync(h_cnt, band_cnt, sizeof(int64_t) * p.B, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         memcpy(cnt_copy, h_cnt, sizeof(int64_t) * p.B);
-        CK(cudaEventRecord(ctx->ev[1], st));
+        CK(stage_mark(ctx, 1, st));
         if ((rc = bucket_tables())) return rc;
         CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * p.G, st));
         CK(launch_bucket_hist(p, J.r, J.phi, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)cnt, st));
@@ -616,7 +641,7 @@ static int begin_common(hrg_ctx *ctx, hrg_job &J, bool sampled, const hrg_params
     if (!pms64 && (rc = ensure(ctx, hrg_ctx::W_SMALL, small_bytes(n), &recs))) return rc;
     CK(launch_scatter_soa(p, (int32_t *)gbuf, (int32_t *)slot, (int32_t *)start, J.r, J.phi, (PointRec *)recs,
                           (uint64_t *)A, (PMS *)pms, (PMS64 *)pms64, (int32_t *)pos_of, st));
-    CK(cudaEventRecord(ctx->ev[2], st));
+    CK(stage_mark(ctx, 2, st));
     // the exact band counts (read back behind the scan and the scatter): hub
     // queries and empty innermost bands
     if (sampled) {
@@ -818,14 +843,14 @@ extern "C" int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_p
 
     // 1. points
     const Plan *P = (const Plan *)d_plans;
-    CK(cudaEventRecord(ctx->ev[0], st));
+    CK(stage_mark(ctx, 0, st));
     CK(launch_graph_of(P, count, (int32_t *)graph_of, st));
     CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * G, st));
     CK(launch_sample_bucket_batch(P, (int32_t *)graph_of, N, r_out, phi_out, (int32_t *)gbuf, (int32_t *)slot,
                                   (int32_t *)cnt, st));
     J.r = r_out;
     J.phi = phi_out;
-    CK(cudaEventRecord(ctx->ev[1], st));
+    CK(stage_mark(ctx, 1, st));
 
     // 2. counting sort by (graph, band, angular bucket); hub query list
     CK(scan_i32_to_i32((int32_t *)cnt, (int32_t *)start, G, scanws, st));
@@ -845,7 +870,7 @@ extern "C" int hrg_generate_batch_begin(hrg_ctx *ctx, int32_t count, const hrg_p
         CK(launch_hub_list(P, count, (int32_t *)start, (int32_t *)hub_cnt, (int32_t *)hub_off, (int32_t *)hub_pos,
                            scanws, st, true));
     }
-    CK(cudaEventRecord(ctx->ev[2], st));
+    CK(stage_mark(ctx, 2, st));
 
     // 3. degrees, 4. row offsets
     QueryBufs &b = J.qb;
@@ -980,17 +1005,17 @@ extern "C" int hrg_update_begin(hrg_ctx *ctx, int64_t n, double R, double *r, do
     const Plan &p = J.plan;
     CK(launch_move_query(p, b, J.fp64, false, k, ids, (uint32_t *)moved, (int32_t *)deg, (int32_t *)gain, nullptr,
                          nullptr, nullptr, st));
-    CK(cudaEventRecord(ctx->ev[3], st));
+    CK(stage_mark(ctx, 3, st));
     CK(launch_move_removed(k, ids, row_off, col_idx, (uint32_t *)moved, (int32_t *)rem, st));
     MoveLists ml{{(int32_t *)lists[0], (int32_t *)lists[1], (int32_t *)lists[2]}};
     void *rows_ws;
     if ((rc = ensure(ctx, hrg_ctx::W_MVWS, move_rows_ws_bytes(on - o0), &rows_ws))) return rc;
     CK(launch_move_degrees(n, on - o0, row_off, (uint32_t *)moved, (int32_t *)rem, (int32_t *)gain, (int32_t *)deg,
                            (int32_t *)keep, ml, (int32_t *)listcnt, (unsigned long long *)bigtot, rows_ws, st));
-    CK(cudaEventRecord(ctx->ev[4], st));
+    CK(stage_mark(ctx, 4, st));
     // 4. row offsets
     CK(scan_i32_to_i64((int32_t *)deg, row_off_out, n, scanws, st));
-    CK(cudaEventRecord(ctx->ev[5], st));
+    CK(stage_mark(ctx, 5, st));
     CK(cudaMemcpyAsync(hp + 0, row_off_out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(hp + 8, listcnt, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(hp + 24, bigtot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -1013,11 +1038,11 @@ static int update_finish(hrg_job *job, int32_t *col_out)
     cudaStream_t st = job->stream;
     const Plan &p = job->plan;
     const int64_t n = p.n;
-    CK(cudaEventRecord(ctx->ev[6], st));
+    CK(stage_mark(ctx, 6, st));
     CK(cudaMemsetAsync(job->gain_cur, 0, sizeof(int32_t) * n, st));
     CK(launch_move_query(p, job->qb, job->fp64, true, job->moves, job->move_ids, job->moved, nullptr, job->gain_cur,
                          job->keep, job->row_off, col_out, st));
-    CK(cudaEventRecord(ctx->ev[7], st));
+    CK(stage_mark(ctx, 7, st));
     {
         void *start_drop, *ws;
         int rc;
@@ -1026,7 +1051,7 @@ static int update_finish(hrg_job *job, int32_t *col_out)
         CK(launch_move_rows(n, job->old_entries, job->old_off, job->old_col, job->moved, job->rem,
                             (int32_t *)start_drop, ws, job->row_off, col_out, st));
     }
-    CK(cudaEventRecord(ctx->ev[8], st));
+    CK(stage_mark(ctx, 8, st));
     if (job->lists[0] > 0 || job->lists[1] > 0 || job->lists[2] > 0) {
         void *tmp = nullptr, *bws = nullptr;
         int rc;
@@ -1037,7 +1062,7 @@ static int update_finish(hrg_job *job, int32_t *col_out)
         }
         CK(launch_sort_rows(p, job->qb, job->lists, job->big_total, job->row_off, col_out, (int32_t *)tmp, bws, st));
     }
-    CK(cudaEventRecord(ctx->ev[9], st));
+    CK(stage_mark(ctx, 9, st));
     CK(launch_move_check_gains(n, job->gain, job->gain_cur, job->qb.stats + 7, st));
     uint64_t *hs = (uint64_t *)ctx->pinned;
     CK(cudaMemcpyAsync(hs, job->qb.stats + 7, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -1119,7 +1144,7 @@ static int finish_impl(hrg_job *job, int32_t *col_idx_out, const HostCol *hc)
         sub_tot[0] = job->big_total;
     }
     cudaEvent_t *cev = ctx->hev + 3;
-    CK(cudaEventRecord(ctx->ev[6], st));
+    CK(stage_mark(ctx, 6, st));
     if (job->p_hub > 0) CK(cudaMemsetAsync(job->qb.cursor, 0, sizeof(int32_t) * job->p_hub, st));
     for (int k = 0; k < K; ++k) {
         const int64_t lo = bounds[k], hi = bounds[k + 1];
@@ -1129,9 +1154,9 @@ static int finish_impl(hrg_job *job, int32_t *col_idx_out, const HostCol *hc)
                                st));
         else
             CK(launch_write_hub(p, job->qb, job->fp64, job->p_hub, job->row_off, col_idx_out, st));
-        CK(cudaEventRecord(K > 1 ? cev[4 * k + 1] : ctx->ev[7], st));
+        CK(K > 1 ? cudaEventRecord(cev[4 * k + 1], st) : stage_mark(ctx, 7, st));
         CK(launch_write_rim(p, job->qb, job->fp64, job->row_off, col_idx_out, lo, hi, st));
-        CK(cudaEventRecord(K > 1 ? cev[4 * k + 2] : ctx->ev[8], st));
+        CK(K > 1 ? cudaEventRecord(cev[4 * k + 2], st) : stage_mark(ctx, 8, st));
         const int32_t *cnt = sub_cnt + 3 * k;
         if (cnt[0] > 0 || cnt[1] > 0 || cnt[2] > 0) {
             QueryBufs bc = job->qb;
@@ -1154,7 +1179,7 @@ static int finish_impl(hrg_job *job, int32_t *col_idx_out, const HostCol *hc)
                                cudaMemcpyDeviceToHost, hc->copy));
         }
     }
-    CK(cudaEventRecord(ctx->ev[9], st));
+    CK(stage_mark(ctx, 9, st));
     uint64_t *hs = (uint64_t *)ctx->pinned;
     CK(cudaMemcpyAsync(hs, job->qb.stats + 7, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

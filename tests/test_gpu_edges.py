@@ -253,4 +253,44 @@ def test_limits_rejected(ctx):
     assert L.hrg_set_limits(ctx.h, ctypes.byref(bad)) == H.HRG_EINVAL
     bad = H.hrg_limits(0, 1 << 40, 0, 0)
     assert L.hrg_set_limits(ctx.h, ctypes.byref(bad)) == H.HRG_EINVAL
+    bad = H.hrg_limits(0, 0, 0, 0, -1)
+    assert L.hrg_set_limits(ctx.h, ctypes.byref(bad)) == H.HRG_EINVAL
     assert L.hrg_set_limits(ctx.h, None) == H.HRG_OK
+
+
+def test_workspace_cap_gives_enomem_and_the_context_recovers(ctx):
+    """A device allocation that fails (forced here by a cap on the context's
+    workspace, on the host, with no GPU fault) returns HRG_ENOMEM; the
+    context then generates the same graph once the cap is lifted."""
+    w = W.scaled(W.MEDIUM, 100_000)
+    ref = H.Context(0)
+    c = H.Context(0)
+    try:
+        a = H.generate(ref, w.n, w.alpha, w.kbar, w.seed)
+        for cap in (1 << 20, 6 << 20):  # the first allocation, then one part-way through
+            c.set_limits(workspace_bytes=cap)
+            with pytest.raises(H.HrgError) as e:
+                H.generate(c, w.n, w.alpha, w.kbar, w.seed)
+            assert e.value.code == H.HRG_ENOMEM
+            assert c.workspace_bytes() <= cap
+        c.set_limits()
+        b = H.generate(c, w.n, w.alpha, w.kbar, w.seed)
+        for k in ("r", "phi", "row_off", "col_idx"):
+            assert torch.equal(a[k], b[k]), k
+        # a larger graph under a cap below what the context already holds
+        # fails at its first growing buffer; the workspace given back and the
+        # cap raised, it runs
+        w2 = W.scaled(W.MEDIUM, 200_000)
+        a2 = H.generate(ref, w2.n, w2.alpha, w2.kbar, w2.seed)
+        c.set_limits(workspace_bytes=c.workspace_bytes() // 2)
+        with pytest.raises(H.HrgError) as e:
+            H.generate(c, w2.n, w2.alpha, w2.kbar, w2.seed)
+        assert e.value.code == H.HRG_ENOMEM
+        c.release_workspace()
+        assert c.workspace_bytes() == 0
+        c.set_limits(workspace_bytes=4 << 30)
+        b2 = H.generate(c, w2.n, w2.alpha, w2.kbar, w2.seed)
+        assert torch.equal(a2["row_off"], b2["row_off"]) and torch.equal(a2["col_idx"], b2["col_idx"])
+    finally:
+        c.close()
+        ref.close()
